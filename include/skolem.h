@@ -1,0 +1,138 @@
+/*
+ * skolem.h -- C ABI of libskolem.so, a GB300 (sm_103a) library that counts
+ * Skolem, Langford and hooked Skolem pairings exactly, after "Counting Skolem
+ * Sequences" (Assarpour, Bar-Noy, Liu), Sec. 2, and approximately by
+ * parallel tempering, Sec. 3.
+ *
+ * Problems (variant):
+ *   SK_SKOLEM   -- Sec. 1.1: split {1..2n} into n pairs (a_k, b_k) with
+ *                  b_k - a_k = k.
+ *   SK_LANGFORD -- Sec. 1.1: arrange 1,1,2,2,..,n,n so the two copies of k have
+ *                  k numbers between them (positions k+1 apart).
+ *   SK_HOOKED   -- Sec. 1.2: split {1..2n-1, 2n+1} into n pairs with
+ *                  differences 1..n.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status (SK_OK = 0 or a negative SK_E*
+ *     code) and writes its out-parameters only on SK_OK.
+ *   - The caller owns every pointer it passes; the library never returns
+ *     memory it allocated.  Pointers documented as "host" are host memory;
+ *     pointers documented as "device" are device memory of the current CUDA
+ *     device (for example torch tensors' data pointers).
+ *   - `stream` fields are cudaStream_t values passed as void*; NULL selects a
+ *     stream private to the library.  Calls are synchronous with respect to
+ *     the host unless stated otherwise.
+ *   - Zero is a valid count: n outside the existence classes returns 0 with
+ *     SK_OK (Sec. 1.1: Skolem pairings exist iff n = 0,1 mod 4, Langford iff
+ *     n = 0,3 mod 4).
+ *   - The library needs a CUDA device of compute capability 10.3; without one
+ *     every computing call returns SK_ECUDA.  There is no CPU fallback.
+ */
+#ifndef SKOLEM_H
+#define SKOLEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { SK_SKOLEM = 0, SK_LANGFORD = 1, SK_HOOKED = 2 };
+
+enum {
+  SK_OK = 0,
+  SK_EINVAL = -1,     /* bad argument: variant, n, pointer, option */
+  SK_ERANGE = -2,     /* the moduli cannot represent the value */
+  SK_ECUDA = -3,      /* CUDA error or no usable device */
+  SK_ENOMEM = -4,     /* device or host allocation failed */
+  SK_ETIMEOUT = -5,   /* a bounded device loop gave up (error word set) */
+  SK_EMISMATCH = -6,  /* a consistency check failed (check prime, 2^{2n-1}
+                         divisibility, sign, parity of the count) */
+  SK_ECKPT = -7       /* checkpoint file unreadable, corrupt or for another job */
+};
+
+/* Output conventions of the exact count.  Sec. 1.3: OEIS A059106 / A014552
+ * (Tables 4, 5, 7, 8 of the paper) identify a sequence with its reflection;
+ * A004075 / A176127 count both.  Lemma 2.1 yields the latter. */
+enum { SK_COUNT_REFLECTIONS_IDENTIFIED = 0, SK_COUNT_ALL = 1 };
+
+#define SK_MAX_N 28        /* largest n with a compiled exact kernel */
+#define SK_MAX_PRIMES 4
+
+typedef struct { uint64_t lo, hi; } sk_u128;   /* unsigned 128-bit integer */
+
+/* Options of the exact count; zero-initialise and set what you need. */
+typedef struct sk_count_opts {
+  int nprimes;                 /* 0 -> 3.  3: CRT over 3 moduli.  4: the 4th
+                                  modulus checks the CRT result. */
+  uint64_t primes[SK_MAX_PRIMES]; /* 0 -> built-in 62-bit primes.  Each must be
+                                  odd, in (2^40, 2^62), pairwise coprime. */
+  int convention;              /* SK_COUNT_REFLECTIONS_IDENTIFIED (default) or
+                                  SK_COUNT_ALL */
+  int walk_bits;               /* m: Gray-walk bits per work item; 0 -> planner */
+  int block_threads;           /* 32..256, multiple of 32; 0 -> 256 */
+  int grid;                    /* CTAs; 0 -> SMs x resident CTAs per SM */
+  void *stream;                /* cudaStream_t or NULL */
+  const char *checkpoint_path; /* NULL: no checkpoint.  Else completed chunks
+                                  are appended to this file and skipped when
+                                  the same job is run again. */
+  uint64_t chunk_items;        /* work items per launch; 0 -> all in one launch
+                                  (or ~10 s of work when checkpointing) */
+  uint64_t max_chunks;         /* stop (status SK_OK, report->complete = 0)
+                                  after this many new chunks; 0 = no limit */
+} sk_count_opts;
+
+typedef struct sk_count_report {
+  int nprimes;
+  uint64_t primes[SK_MAX_PRIMES];
+  uint64_t residues[SK_MAX_PRIMES]; /* H mod p_i, H = sum of Lemma 2.1 over the
+                                       2^{2n-1} assignments with x_{max P} = +1 */
+  sk_u128 coefficient;         /* pairings with reflections distinct */
+  uint64_t terms;              /* 2^{2n-1} */
+  uint64_t items;              /* work items (2^{2n-1-m}) */
+  int walk_bits;               /* m */
+  int inner_bits;              /* unrolled Gray bits */
+  int block_threads, grid;
+  uint64_t chunks_total, chunks_done, chunks_resumed;
+  int complete;                /* 1 when every chunk is done */
+  double kernel_ms;            /* device time of the launches of this call */
+  double wall_ms;              /* host time of the whole call */
+} sk_count_report;
+
+/* Exact count of `variant` of order n (Lemma 2.1 with Lemma 2.2, evaluated in
+ * Gray-code order, Sec. 2.1; residues modulo co-primes and the Chinese
+ * remainder theorem, Sec. 2.2).  out (host): the count in the default
+ * convention (reflections identified for Skolem and Langford; the hooked
+ * count as is).  1 <= n <= SK_MAX_N. */
+int skolem_count(int variant, int n, sk_u128 *out);
+
+/* As skolem_count with options and an optional report (host pointers; opts
+ * and rep may be NULL).  With a checkpoint path the call may stop early
+ * (opts->max_chunks) and resume later; out is written only when complete. */
+int skolem_count_ex(int variant, int n, const sk_count_opts *opts, sk_u128 *out,
+                    sk_count_report *rep);
+
+/* Residues of single work items, for sampled checks at full size.  Item q of
+ * walk width m fixes the free variables m..2n-2 (bit b of q set means
+ * x_{m+b+1} = -1) and runs the low m through all values; its sum is
+ * sum sign(X) F(n, X) over that block (Lemma 2.1's summand).  For items
+ * q_lo .. q_lo+count-1, out (host, count x nprimes, row-major) receives each
+ * block sum modulo each prime.  primes (host): nprimes in {3, 4} moduli as in
+ * sk_count_opts.  count <= 2^20. */
+int skolem_item_residues(int variant, int n, int m, uint64_t q_lo, uint64_t count,
+                         int nprimes, const uint64_t *primes, uint64_t *out);
+
+/* The built-in moduli (host, 4 entries): the four largest primes below 2^62. */
+void sk_default_primes(uint64_t *out4);
+
+/* Text for a status code (static storage). */
+const char *sk_strerror(int status);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int sk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SKOLEM_H */

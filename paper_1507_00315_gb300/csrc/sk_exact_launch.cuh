@@ -1,0 +1,150 @@
+// sk_exact_launch.cuh -- the single-job Gray-code kernel and its launcher.
+//
+// One persistent grid (a multiple of the SM count) pulls work items from a
+// device counter, one warp-sized chunk (32 items, one per lane) at a time, so
+// the 32 lanes of a warp always walk the same Gray schedule on different
+// prefixes.  Each thread keeps its residues, the warp combines them with
+// shuffles, and one lane per warp adds them into the job's slots with a
+// compare-and-swap modular add (order independent, so the result is
+// bit-exact whatever the schedule).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "sk_exact.cuh"
+
+namespace sk {
+
+// Scratch words of one launch (device memory, zeroed before the launch).
+struct ExactScratch {
+  unsigned long long counter;            // next chunk of items
+  unsigned long long res[kMaxPrimes];    // residues of the sum, raw
+  unsigned int err;                      // nonzero: a bounded loop gave up
+  unsigned int pad;
+};
+
+struct ExactLaunch {
+  ExactJob job;
+  Primes P;
+  unsigned long long item_lo;            // first item of this launch
+  unsigned long long item_hi;            // one past the last item
+  ExactScratch* scratch;                 // device
+  unsigned long long* item_res;          // optional: [item_hi-item_lo][NPR]
+  int block_threads;
+  int grid;                              // 0: SMs x resident blocks
+  cudaStream_t stream;
+};
+
+constexpr int kCasLimit = 1 << 22;
+
+// Two resident 256-thread CTAs per SM: 128 registers per thread, which holds
+// the n correlations, the window of outer values and the residue
+// accumulators without spills up to n = 28.
+#ifndef SK_EXACT_MIN_BLOCKS
+#define SK_EXACT_MIN_BLOCKS 2
+#endif
+
+__device__ __forceinline__ void atomic_addmod(unsigned long long* addr, unsigned long long v,
+                                              unsigned long long p, unsigned int* err) {
+  if (v == 0) return;
+  unsigned long long old = *((volatile unsigned long long*)addr);
+  for (int it = 0; it < kCasLimit; ++it) {
+    unsigned long long nv = addmod(old, v, p);
+    unsigned long long seen = atomicCAS(addr, old, nv);
+    if (seen == old) return;
+    old = seen;
+  }
+  atomicOr(err, 1u);
+}
+
+template <int NPR>
+__device__ __forceinline__ void warp_flush(unsigned long long (&tot)[NPR], const Primes& P,
+                                           unsigned long long* slots, unsigned int* err) {
+#pragma unroll
+  for (int i = 0; i < NPR; ++i) {
+    unsigned long long v = tot[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      v = addmod(v, __shfl_xor_sync(0xffffffffu, v, o), (unsigned long long)P.pr[i].p);
+    if ((threadIdx.x & 31) == 0) atomic_addmod(&slots[i], v, (unsigned long long)P.pr[i].p, err);
+    tot[i] = 0;
+  }
+}
+
+template <int DELTA, int N, int NPR>
+__global__ void __launch_bounds__(256, SK_EXACT_MIN_BLOCKS) exact_kernel(ExactJob job, Primes P,
+                                                    unsigned long long item_lo,
+                                                    unsigned long long item_hi,
+                                                    ExactScratch* scr,
+                                                    unsigned long long* item_res) {
+  extern __shared__ signed char sk_ws[];
+  const unsigned long long count = item_hi - item_lo;
+  const int lane = threadIdx.x & 31;
+  signed char* ws_col = sk_ws + threadIdx.x;
+  unsigned long long tot[NPR];
+#pragma unroll
+  for (int i = 0; i < NPR; ++i) tot[i] = 0;
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&scr->counter, 32ULL);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= count) break;
+    const unsigned long long it = base + lane;
+    if (it < count) {
+      unsigned long long r[NPR];
+      run_item<DELTA, N, NPR>(job.pres, job.m, item_lo + it, P, ws_col, r);
+#pragma unroll
+      for (int i = 0; i < NPR; ++i) {
+        tot[i] = addmod(tot[i], r[i], (unsigned long long)P.pr[i].p);
+        if (item_res) item_res[it * NPR + i] = r[i];
+      }
+    }
+  }
+  warp_flush<NPR>(tot, P, scr->res, &scr->err);
+}
+
+template <int DELTA, int N, int NPR>
+cudaError_t launch_exact(const ExactLaunch& L) {
+  static int blocks_per_sm[257] = {0};
+  static int sms = 0;
+  const int bt = L.block_threads;
+  const size_t smem = (size_t)ws_len(DELTA, N) * kWsStride;
+  if (bt < 32 || bt > 256 || (bt & 31)) return cudaErrorInvalidValue;
+  int grid = L.grid;
+  if (grid <= 0) {
+    if (!sms) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    if (!blocks_per_sm[bt]) {
+      int nb = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &nb, exact_kernel<DELTA, N, NPR>, bt, smem);
+      if (e != cudaSuccess) return e;
+      blocks_per_sm[bt] = nb > 0 ? nb : 1;
+    }
+    grid = sms * blocks_per_sm[bt];
+    // never more warps than chunks of 32 items
+    unsigned long long chunks = (L.item_hi - L.item_lo + 31) / 32;
+    unsigned long long warps_per_block = (unsigned long long)bt / 32;
+    unsigned long long need = (chunks + warps_per_block - 1) / warps_per_block;
+    if ((unsigned long long)grid > need) grid = (int)(need ? need : 1);
+  }
+  exact_kernel<DELTA, N, NPR><<<grid, bt, smem, L.stream>>>(L.job, L.P, L.item_lo, L.item_hi,
+                                                         L.scratch, L.item_res);
+  return cudaGetLastError();
+}
+
+typedef cudaError_t (*ExactLaunchFn)(const ExactLaunch&);
+
+// Launchers for delta in {0, 1}, n in [1, kMaxN], primes in {3, 4}
+// (null for combinations that were not compiled).
+ExactLaunchFn exact_launcher(int delta, int n, int nprimes);
+
+}  // namespace sk
+
+#define SK_INSTANTIATE_EXACT(N)                                                \
+  template cudaError_t sk::launch_exact<0, N, 3>(const sk::ExactLaunch&);      \
+  template cudaError_t sk::launch_exact<0, N, 4>(const sk::ExactLaunch&);      \
+  template cudaError_t sk::launch_exact<1, N, 3>(const sk::ExactLaunch&);      \
+  template cudaError_t sk::launch_exact<1, N, 4>(const sk::ExactLaunch&);

@@ -1,0 +1,431 @@
+// sk_host_exact.cu -- host runtime of the exact count: work planning (Sec.
+// 2.2: power-of-two splits of the assignments), launches, checkpointed
+// chunks, and the C ABI entry points skolem_count / skolem_count_ex /
+// skolem_item_residues.
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <unistd.h>
+#include <vector>
+
+#include "sk_exact_launch.cuh"
+#include "sk_host_common.h"
+
+namespace sk {
+
+// ------------------------------------------------------------ launcher table
+
+#define SK_EXTERN_EXACT(N)                                                         \
+  extern template cudaError_t launch_exact<0, N, 3>(const ExactLaunch&);          \
+  extern template cudaError_t launch_exact<0, N, 4>(const ExactLaunch&);          \
+  extern template cudaError_t launch_exact<1, N, 3>(const ExactLaunch&);          \
+  extern template cudaError_t launch_exact<1, N, 4>(const ExactLaunch&);
+SK_EXTERN_EXACT(1) SK_EXTERN_EXACT(2) SK_EXTERN_EXACT(3) SK_EXTERN_EXACT(4) SK_EXTERN_EXACT(5)
+SK_EXTERN_EXACT(6) SK_EXTERN_EXACT(7) SK_EXTERN_EXACT(8) SK_EXTERN_EXACT(9) SK_EXTERN_EXACT(10)
+SK_EXTERN_EXACT(11) SK_EXTERN_EXACT(12) SK_EXTERN_EXACT(13) SK_EXTERN_EXACT(14)
+SK_EXTERN_EXACT(15) SK_EXTERN_EXACT(16) SK_EXTERN_EXACT(17) SK_EXTERN_EXACT(18)
+SK_EXTERN_EXACT(19) SK_EXTERN_EXACT(20) SK_EXTERN_EXACT(21) SK_EXTERN_EXACT(22)
+SK_EXTERN_EXACT(23) SK_EXTERN_EXACT(24) SK_EXTERN_EXACT(25) SK_EXTERN_EXACT(26)
+SK_EXTERN_EXACT(27) SK_EXTERN_EXACT(28)
+#undef SK_EXTERN_EXACT
+
+#define SK_ROW(N) {{launch_exact<0, N, 3>, launch_exact<0, N, 4>}, {launch_exact<1, N, 3>, launch_exact<1, N, 4>}}
+static const ExactLaunchFn kTable[kMaxN + 1][2][2] = {
+    {{nullptr, nullptr}, {nullptr, nullptr}},
+    SK_ROW(1), SK_ROW(2), SK_ROW(3), SK_ROW(4), SK_ROW(5), SK_ROW(6), SK_ROW(7),
+    SK_ROW(8), SK_ROW(9), SK_ROW(10), SK_ROW(11), SK_ROW(12), SK_ROW(13), SK_ROW(14),
+    SK_ROW(15), SK_ROW(16), SK_ROW(17), SK_ROW(18), SK_ROW(19), SK_ROW(20), SK_ROW(21),
+    SK_ROW(22), SK_ROW(23), SK_ROW(24), SK_ROW(25), SK_ROW(26), SK_ROW(27), SK_ROW(28)};
+#undef SK_ROW
+
+ExactLaunchFn exact_launcher(int delta, int n, int nprimes) {
+  if (delta < 0 || delta > 1 || n < 1 || n > kMaxN || nprimes < 3 || nprimes > 4) return nullptr;
+  return kTable[n][delta][nprimes - 3];
+}
+
+// ------------------------------------------------------------ planning
+
+// Position set of Sec. 1.1 / 1.2 as a bit mask (bit i = position i+1).
+unsigned long long position_mask(int variant, int n) {
+  if (variant == SK_HOOKED) {
+    unsigned long long all = (n >= 32) ? ~0ULL : ((1ULL << (2 * n + 1)) - 1);
+    return all & ~(1ULL << (2 * n - 1));
+  }
+  return (1ULL << (2 * n)) - 1;
+}
+
+int default_walk_bits(int n) {
+  const int F = 2 * n - 1;
+  const int U = inner_bits(n);
+  // aim at 2^22 items (2^24 for the largest orders) so a persistent grid of
+  // ~80k threads gets dozens of items each and the tail stays short
+  int m = F - (n >= 22 ? 24 : 22);
+  if (m < U + 4) m = U + 4;
+  if (m > F) m = F;
+  if (m < U) m = U;
+  return m;
+}
+
+struct Plan {
+  int variant, n, delta, m, U, nprimes, block_threads, grid;
+  unsigned long long pres, items;
+  uint64_t primes[kMaxPrimes];
+  Primes P;
+  ExactLaunchFn fn;
+};
+
+static int make_plan(int variant, int n, const sk_count_opts* o, Plan* pl) {
+  if (variant < SK_SKOLEM || variant > SK_HOOKED || n < 1 || n > kMaxN) return SK_EINVAL;
+  std::memset(pl, 0, sizeof(*pl));
+  pl->variant = variant;
+  pl->n = n;
+  pl->delta = (variant == SK_LANGFORD) ? 1 : 0;
+  int st = prepare_primes(o, &pl->nprimes, pl->primes, &pl->P);
+  if (st) return st;
+  const int F = 2 * n - 1;
+  pl->U = inner_bits(n);
+  pl->m = (o && o->walk_bits) ? o->walk_bits : default_walk_bits(n);
+  if (pl->m < pl->U || pl->m > F || F - pl->m > 40) return SK_EINVAL;
+  pl->items = 1ULL << (F - pl->m);
+  pl->pres = position_mask(variant, n);
+  pl->block_threads = (o && o->block_threads) ? o->block_threads : 256;
+  if (pl->block_threads < 32 || pl->block_threads > 256 || (pl->block_threads & 31)) return SK_EINVAL;
+  pl->grid = (o && o->grid > 0) ? o->grid : 0;
+  pl->fn = exact_launcher(pl->delta, n, pl->nprimes);
+  if (!pl->fn) return SK_EINVAL;
+  return SK_OK;
+}
+
+// Multiplies raw residues by R^{e}, e = groups - 2, removing the Montgomery
+// factor every term carries.
+static void unmont(const Plan& pl, uint64_t* res) {
+  GroupInfo gi = make_groups(pl.delta, pl.n);
+  int e = gi.g > 2 ? gi.g - 2 : 0;
+  for (int i = 0; i < pl.nprimes; ++i) {
+    uint64_t R = ((u128)1 << 32) % pl.primes[i];
+    res[i] = mulmod(res[i] % pl.primes[i], powmod(R, (uint64_t)e, pl.primes[i]), pl.primes[i]);
+  }
+}
+
+// One launch over items [lo, hi): raw residues into res (host).
+static int run_chunk(const Plan& pl, unsigned long long lo, unsigned long long hi,
+                     ExactScratch* dscr, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1,
+                     uint64_t* res, double* kernel_ms, unsigned long long* item_res,
+                     int* grid_used) {
+  cudaError_t e = cudaMemsetAsync(dscr, 0, sizeof(ExactScratch), st);
+  if (e != cudaSuccess) return cuda_status(e);
+  ExactLaunch L;
+  L.job.pres = pl.pres;
+  L.job.items = pl.items;
+  L.job.m = pl.m;
+  L.job.job = 0;
+  L.P = pl.P;
+  L.item_lo = lo;
+  L.item_hi = hi;
+  L.scratch = dscr;
+  L.item_res = item_res;
+  L.block_threads = pl.block_threads;
+  L.grid = pl.grid;
+  L.stream = st;
+  cudaEventRecord(e0, st);
+  e = pl.fn(L);
+  if (e != cudaSuccess) return cuda_status(e);
+  cudaEventRecord(e1, st);
+  ExactScratch h;
+  e = cudaMemcpyAsync(&h, dscr, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  *kernel_ms += ms;
+  if (h.err) return SK_ETIMEOUT;
+  for (int i = 0; i < pl.nprimes; ++i) res[i] = h.res[i];
+  if (grid_used) *grid_used = pl.grid;
+  return SK_OK;
+}
+
+// ------------------------------------------------------------ checkpoint
+
+struct Ckpt {
+  std::string path;
+  std::string header;
+  std::vector<int> have;                 // per chunk: 1 if done
+  std::vector<uint64_t> res;             // per chunk: nprimes residues
+};
+
+static std::string ckpt_header(const Plan& pl, unsigned long long chunk_items,
+                               unsigned long long nchunks) {
+  char buf[512];
+  std::snprintf(buf, sizeof(buf), "SKCKPT1 v=%d n=%d m=%d k=%d p=%llu,%llu,%llu,%llu items=%llu chunk=%llu chunks=%llu",
+                pl.variant, pl.n, pl.m, pl.nprimes, (unsigned long long)pl.primes[0],
+                (unsigned long long)pl.primes[1], (unsigned long long)pl.primes[2],
+                (unsigned long long)(pl.nprimes > 3 ? pl.primes[3] : 0), pl.items, chunk_items,
+                nchunks);
+  return std::string(buf);
+}
+
+// Reads an existing checkpoint; a missing file is an empty checkpoint.  A
+// final line without its newline is a torn write and is ignored.
+static int ckpt_load(Ckpt* ck, const Plan& pl) {
+  FILE* f = std::fopen(ck->path.c_str(), "rb");
+  if (!f) return SK_OK;
+  std::string all;
+  char buf[4096];
+  size_t r;
+  while ((r = std::fread(buf, 1, sizeof(buf), f)) > 0) all.append(buf, r);
+  std::fclose(f);
+  size_t pos = 0;
+  bool first = true;
+  while (pos < all.size()) {
+    size_t nl = all.find('\n', pos);
+    if (nl == std::string::npos) {        // torn tail: cut it off so the next
+      if (truncate(ck->path.c_str(), (off_t)pos) != 0) return SK_ECKPT;  // append starts clean
+      break;
+    }
+    std::string line = all.substr(pos, nl - pos);
+    pos = nl + 1;
+    if (first) {
+      if (line != ck->header) return SK_ECKPT;
+      first = false;
+      continue;
+    }
+    unsigned long long idx = 0, v[4] = {0, 0, 0, 0};
+    unsigned crc = 0;
+    int got = std::sscanf(line.c_str(), "chunk %llu %llu %llu %llu %llu crc=%x", &idx, &v[0], &v[1],
+                          &v[2], &v[3], &crc);
+    if (got != 6) return SK_ECKPT;
+    size_t cpos = line.find(" crc=");
+    if (cpos == std::string::npos || crc32(line.data(), cpos) != crc) return SK_ECKPT;
+    if (idx >= ck->have.size()) return SK_ECKPT;
+    for (int i = 0; i < pl.nprimes; ++i)
+      if (v[i] >= pl.primes[i]) return SK_ECKPT;
+    if (ck->have[idx]) {
+      for (int i = 0; i < pl.nprimes; ++i)
+        if (ck->res[idx * pl.nprimes + i] != v[i]) return SK_ECKPT;
+    }
+    ck->have[idx] = 1;
+    for (int i = 0; i < pl.nprimes; ++i) ck->res[idx * pl.nprimes + i] = v[i];
+  }
+  return SK_OK;
+}
+
+static int ckpt_append(const Ckpt& ck, bool write_header, unsigned long long idx,
+                       const uint64_t* v, int k) {
+  FILE* f = std::fopen(ck.path.c_str(), "ab");
+  if (!f) return SK_ECKPT;
+  char line[512];
+  int len = std::snprintf(line, sizeof(line), "chunk %llu %llu %llu %llu %llu", idx,
+                          (unsigned long long)v[0], (unsigned long long)v[1],
+                          (unsigned long long)v[2], (unsigned long long)(k > 3 ? v[3] : 0));
+  uint32_t crc = crc32(line, (size_t)len);
+  int ok = 1;
+  if (write_header) ok &= std::fprintf(f, "%s\n", ck.header.c_str()) > 0;
+  ok &= std::fprintf(f, "%s crc=%08x\n", line, crc) > 0;
+  ok &= std::fflush(f) == 0;
+  ok &= fsync(fileno(f)) == 0;
+  std::fclose(f);
+  return ok ? SK_OK : SK_ECKPT;
+}
+
+// ------------------------------------------------------------ count
+
+static void u128_half(sk_u128* v) {
+  v->lo = (v->lo >> 1) | (v->hi << 63);
+  v->hi >>= 1;
+}
+
+int count_impl(int variant, int n, const sk_count_opts* o, sk_u128* out, sk_count_report* rep) {
+  auto t0 = std::chrono::steady_clock::now();
+  Plan pl;
+  int st = make_plan(variant, n, o, &pl);
+  if (st) return st;
+  if (o && o->convention != SK_COUNT_REFLECTIONS_IDENTIFIED && o->convention != SK_COUNT_ALL)
+    return SK_EINVAL;
+  st = check_device();
+  if (st) return st;
+  cudaStream_t stream = (o && o->stream) ? (cudaStream_t)o->stream : nullptr;
+  bool own_stream = false;
+  if (!stream) {
+    if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) return SK_ECUDA;
+    own_stream = true;
+  }
+  const bool ckpt_on = o && o->checkpoint_path && o->checkpoint_path[0];
+  unsigned long long chunk = (o && o->chunk_items) ? o->chunk_items : 0;
+  if (!chunk) {
+    if (ckpt_on) {
+      // about 2^37 terms per launch (~1 s on one GB300 at n = 24)
+      int lg = 37 - pl.m;
+      chunk = lg <= 0 ? 1ULL : (lg >= 40 ? pl.items : (1ULL << lg));
+    } else {
+      chunk = pl.items;
+    }
+  }
+  if (chunk > pl.items) chunk = pl.items;
+  const unsigned long long nchunks = (pl.items + chunk - 1) / chunk;
+  Ckpt ck;
+  ck.have.assign(ckpt_on ? nchunks : 0, 0);
+  ck.res.assign(ckpt_on ? nchunks * pl.nprimes : 0, 0);
+  uint64_t resumed = 0;
+  bool file_exists = false;
+  if (ckpt_on) {
+    ck.path = o->checkpoint_path;
+    ck.header = ckpt_header(pl, chunk, nchunks);
+    st = ckpt_load(&ck, pl);
+    if (st) { if (own_stream) cudaStreamDestroy(stream); return st; }
+    FILE* f = std::fopen(ck.path.c_str(), "rb");
+    if (f) {
+      std::fseek(f, 0, SEEK_END);
+      file_exists = std::ftell(f) > 0;
+      std::fclose(f);
+    }
+    for (auto h : ck.have) resumed += h;
+  }
+
+  ExactScratch* dscr = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaMalloc(&dscr, sizeof(ExactScratch));
+  if (ce != cudaSuccess) { if (own_stream) cudaStreamDestroy(stream); return cuda_status(ce); }
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  uint64_t H[kMaxPrimes] = {0, 0, 0, 0};
+  double kms = 0.0;
+  uint64_t done_new = 0, done_total = resumed;
+  const uint64_t max_new = (o && o->max_chunks) ? o->max_chunks : 0;
+  for (unsigned long long c = 0; c < nchunks && st == SK_OK; ++c) {
+    uint64_t r[kMaxPrimes] = {0, 0, 0, 0};
+    if (ckpt_on && ck.have[c]) {
+      for (int i = 0; i < pl.nprimes; ++i) r[i] = ck.res[c * pl.nprimes + i];
+    } else {
+      if (max_new && done_new >= max_new) continue;
+      unsigned long long lo = c * chunk, hi = lo + chunk < pl.items ? lo + chunk : pl.items;
+      st = run_chunk(pl, lo, hi, dscr, stream, e0, e1, r, &kms, nullptr, nullptr);
+      if (st) break;
+      if (ckpt_on) {
+        st = ckpt_append(ck, !file_exists, c, r, pl.nprimes);
+        file_exists = true;
+        if (st) break;
+        ck.have[c] = 1;
+      }
+      ++done_new;
+      ++done_total;
+    }
+    for (int i = 0; i < pl.nprimes; ++i) H[i] = (H[i] + r[i]) % pl.primes[i];
+  }
+  cudaFree(dscr);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (own_stream) cudaStreamDestroy(stream);
+  if (st) return st;
+  const bool complete = done_total == nchunks;
+  unmont(pl, H);
+  sk_u128 coeff = {0, 0};
+  if (complete) {
+    st = crt_coefficient(n, pl.nprimes, pl.primes, H, &coeff);
+    if (st) return st;
+  }
+  if (rep) {
+    std::memset(rep, 0, sizeof(*rep));
+    rep->nprimes = pl.nprimes;
+    for (int i = 0; i < pl.nprimes; ++i) {
+      rep->primes[i] = pl.primes[i];
+      rep->residues[i] = complete ? H[i] : 0;
+    }
+    rep->coefficient = coeff;
+    rep->terms = 1ULL << (2 * n - 1);
+    rep->items = pl.items;
+    rep->walk_bits = pl.m;
+    rep->inner_bits = pl.U;
+    rep->block_threads = pl.block_threads;
+    rep->grid = pl.grid;
+    rep->chunks_total = nchunks;
+    rep->chunks_done = done_total;
+    rep->chunks_resumed = resumed;
+    rep->complete = complete ? 1 : 0;
+    rep->kernel_ms = kms;
+    rep->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (!complete) return SK_OK;
+  sk_u128 v = coeff;
+  const int conv = o ? o->convention : SK_COUNT_REFLECTIONS_IDENTIFIED;
+  if (conv == SK_COUNT_REFLECTIONS_IDENTIFIED && variant != SK_HOOKED) {
+    // Sec. 1.3: no sequence of order n > 1 is its own reflection; the single
+    // Skolem sequence of order 1 (1,1) is.
+    if (variant == SK_SKOLEM && n == 1) {
+      v.lo += 1;
+    } else if (v.lo & 1) {
+      return SK_EMISMATCH;
+    }
+    u128_half(&v);
+  }
+  if (out) *out = v;
+  return SK_OK;
+}
+
+int item_residues_impl(int variant, int n, int m, uint64_t q_lo, uint64_t count, int nprimes,
+                       const uint64_t* primes, uint64_t* out) {
+  if (!out || !primes || count == 0 || count > (1ULL << 20)) return SK_EINVAL;
+  sk_count_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.nprimes = nprimes;
+  for (int i = 0; i < nprimes && i < SK_MAX_PRIMES; ++i) o.primes[i] = primes[i];
+  o.walk_bits = m;
+  Plan pl;
+  int st = make_plan(variant, n, &o, &pl);
+  if (st) return st;
+  if (q_lo >= pl.items || count > pl.items - q_lo) return SK_EINVAL;
+  st = check_device();
+  if (st) return st;
+  cudaStream_t stream;
+  if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) return SK_ECUDA;
+  ExactScratch* dscr = nullptr;
+  unsigned long long* dres = nullptr;
+  cudaError_t ce = cudaMalloc(&dscr, sizeof(ExactScratch));
+  if (ce == cudaSuccess) ce = cudaMalloc(&dres, count * pl.nprimes * sizeof(unsigned long long));
+  if (ce != cudaSuccess) {
+    cudaFree(dscr);
+    cudaStreamDestroy(stream);
+    return cuda_status(ce);
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  uint64_t r[kMaxPrimes];
+  double kms = 0;
+  st = run_chunk(pl, q_lo, q_lo + count, dscr, stream, e0, e1, r, &kms, dres, nullptr);
+  std::vector<uint64_t> h(count * pl.nprimes);
+  if (!st) {
+    ce = cudaMemcpy(h.data(), dres, h.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) st = cuda_status(ce);
+  }
+  cudaFree(dscr);
+  cudaFree(dres);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(stream);
+  if (st) return st;
+  for (uint64_t q = 0; q < count; ++q) {
+    unmont(pl, &h[q * pl.nprimes]);
+    for (int i = 0; i < pl.nprimes; ++i) out[q * pl.nprimes + i] = h[q * pl.nprimes + i];
+  }
+  return SK_OK;
+}
+
+}  // namespace sk
+
+extern "C" int skolem_count(int variant, int n, sk_u128* out) {
+  if (!out) return SK_EINVAL;
+  return sk::count_impl(variant, n, nullptr, out, nullptr);
+}
+
+extern "C" int skolem_count_ex(int variant, int n, const sk_count_opts* opts, sk_u128* out,
+                               sk_count_report* rep) {
+  return sk::count_impl(variant, n, opts, out, rep);
+}
+
+extern "C" int skolem_item_residues(int variant, int n, int m, uint64_t q_lo, uint64_t count,
+                                    int nprimes, const uint64_t* primes, uint64_t* out) {
+  return sk::item_residues_impl(variant, n, m, q_lo, count, nprimes, primes, out);
+}
