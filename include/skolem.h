@@ -122,6 +122,13 @@ int skolem_count_ex(int variant, int n, const sk_count_opts *opts, sk_u128 *out,
 int skolem_item_residues(int variant, int n, int m, uint64_t q_lo, uint64_t count,
                          int nprimes, const uint64_t *primes, uint64_t *out);
 
+/* INT32 throughput of the current device, the denominator of the exact
+ * kernel's roofline (that path is integer-ALU bound).  mode 0: independent
+ * 32-bit multiply-adds; mode 1: multiply-adds interleaved with three-input
+ * logic ops.  ops_per_s (host): 32-bit operations per second; ms (host, may
+ * be NULL): duration of the timed launch. */
+int sk_int32_peak(int mode, double *ops_per_s, double *ms);
+
 /* The built-in moduli (host, 4 entries): the four largest primes below 2^62. */
 void sk_default_primes(uint64_t *out4);
 

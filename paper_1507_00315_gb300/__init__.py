@@ -95,6 +95,8 @@ def lib():
                                            ctypes.c_uint64, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_uint64),
                                            ctypes.POINTER(ctypes.c_uint64)]
+        L.sk_int32_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double)]
         L.sk_default_primes.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
         L.sk_default_primes.restype = None
         L.sk_strerror.argtypes = [ctypes.c_int]
@@ -162,6 +164,15 @@ def count_ex(variant, n: int, **kw):
         raise SkolemError(st, f"skolem_count_ex({variant}, {n})")
     r = rep.as_dict()
     return (out.value() if r["complete"] else None), r
+
+
+def int32_peak(mode: int = 0):
+    """sk_int32_peak: (ops per second, ms of the timed launch)."""
+    v, ms = ctypes.c_double(), ctypes.c_double()
+    st = lib().sk_int32_peak(mode, ctypes.byref(v), ctypes.byref(ms))
+    if st != SK_OK:
+        raise SkolemError(st, "sk_int32_peak")
+    return v.value, ms.value
 
 
 def item_residues(variant, n: int, m: int, q_lo: int, count_: int, primes):
