@@ -122,6 +122,27 @@ int skolem_count_ex(int variant, int n, const sk_count_opts *opts, sk_u128 *out,
 int skolem_item_residues(int variant, int n, int m, uint64_t q_lo, uint64_t count,
                          int nprimes, const uint64_t *primes, uint64_t *out);
 
+/* Largest `count` accepted by skolem_item_residues_noalloc: its static device
+ * scratch holds this many work items x SK_MAX_PRIMES residues (512 KiB) plus
+ * one 256-byte launch record. */
+#define SK_NOALLOC_MAX_ITEMS 16384
+
+/* skolem_item_residues for callers that cannot let the library allocate
+ * device memory (a framework whose caching allocator owns the device budget,
+ * or a host loop that cannot absorb the device-wide synchronisation of
+ * cudaFree).  The paper has no counterpart; this is an engineering variant.
+ * Same arguments and results as skolem_item_residues, plus `stream`
+ * (cudaStream_t or NULL for the legacy default stream; the call synchronises
+ * it).  It calls no cudaMalloc / cudaFree and creates no stream or event: its
+ * device scratch is one static array of fixed size in the library, held by
+ * every GPU that loads the library until exit.  The first call on a device
+ * looks up that array's device address (make it before any stream capture).
+ * Every call shares the array: calls that overlap on the GPU race.  count >
+ * SK_NOALLOC_MAX_ITEMS returns SK_EINVAL. */
+int skolem_item_residues_noalloc(int variant, int n, int m, uint64_t q_lo, uint64_t count,
+                                 int nprimes, const uint64_t *primes, void *stream,
+                                 uint64_t *out);
+
 /* INT32 throughput of the current device, the denominator of the exact
  * kernel's roofline (that path is integer-ALU bound).  mode 0: independent
  * 32-bit multiply-adds; mode 1: multiply-adds interleaved with three-input

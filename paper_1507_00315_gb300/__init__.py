@@ -18,6 +18,7 @@ VARIANTS = {"skolem": SKOLEM, "langford": LANGFORD, "hooked": HOOKED}
 REFLECTIONS_IDENTIFIED, COUNT_ALL = 0, 1
 MAX_N = 28
 MAX_PRIMES = 4
+NOALLOC_MAX_ITEMS = 16384
 
 SK_OK, SK_EINVAL, SK_ERANGE, SK_ECUDA, SK_ENOMEM, SK_ETIMEOUT, SK_EMISMATCH, SK_ECKPT = \
     0, -1, -2, -3, -4, -5, -6, -7
@@ -95,6 +96,9 @@ def lib():
                                            ctypes.c_uint64, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_uint64),
                                            ctypes.POINTER(ctypes.c_uint64)]
+        L.skolem_item_residues_noalloc.argtypes = [
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+            ctypes.POINTER(ctypes.c_uint64), ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]
         L.sk_int32_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double)]
         L.sk_default_primes.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
@@ -183,4 +187,17 @@ def item_residues(variant, n: int, m: int, q_lo: int, count_: int, primes):
     st = lib().skolem_item_residues(_variant(variant), n, m, q_lo, count_, k, P, out)
     if st != SK_OK:
         raise SkolemError(st, "skolem_item_residues")
+    return [list(out[i * k:(i + 1) * k]) for i in range(count_)]
+
+
+def item_residues_noalloc(variant, n: int, m: int, q_lo: int, count_: int, primes, stream=None):
+    """skolem_item_residues_noalloc: as item_residues, with no device
+    allocation inside the library (static scratch, at most NOALLOC_MAX_ITEMS
+    items per call)."""
+    k = len(primes)
+    P = (ctypes.c_uint64 * k)(*primes)
+    out = (ctypes.c_uint64 * (count_ * k))()
+    st = lib().skolem_item_residues_noalloc(_variant(variant), n, m, q_lo, count_, k, P, stream, out)
+    if st != SK_OK:
+        raise SkolemError(st, "skolem_item_residues_noalloc")
     return [list(out[i * k:(i + 1) * k]) for i in range(count_)]
