@@ -57,6 +57,14 @@ enum {
 enum { SK_COUNT_REFLECTIONS_IDENTIFIED = 0, SK_COUNT_ALL = 1 };
 
 #define SK_MAX_N 28        /* largest n with a compiled exact kernel */
+
+/* Arithmetic form of the term products (both give identical residues).
+ * SK_ARITH_LIMBS: every term's product is formed exactly in 32-bit limbs
+ * (|prod c_k| <= prod_k L_k, L_k = number of pairs at distance d_k) and added
+ * into an exact accumulator; each work item's sum is reduced modulo the
+ * primes once.  SK_ARITH_MONTGOMERY: every term's product is formed modulo
+ * each prime by signed Montgomery steps (R = 2^32). */
+enum { SK_ARITH_LIMBS = 0, SK_ARITH_MONTGOMERY = 1 };
 #define SK_MAX_PRIMES 4
 
 typedef struct { uint64_t lo, hi; } sk_u128;   /* unsigned 128-bit integer */
@@ -66,7 +74,9 @@ typedef struct sk_count_opts {
   int nprimes;                 /* 0 -> 3.  3: CRT over 3 moduli.  4: the 4th
                                   modulus checks the CRT result. */
   uint64_t primes[SK_MAX_PRIMES]; /* 0 -> built-in 62-bit primes.  Each must be
-                                  odd, in (2^40, 2^62), pairwise coprime. */
+                                  odd, in (2^62 - 2^31, 2^62) (the kernel's
+                                  Montgomery step uses a high limb of 2^30),
+                                  pairwise coprime. */
   int convention;              /* SK_COUNT_REFLECTIONS_IDENTIFIED (default) or
                                   SK_COUNT_ALL */
   int walk_bits;               /* m: Gray-walk bits per work item; 0 -> planner */
@@ -80,6 +90,7 @@ typedef struct sk_count_opts {
                                   (or ~10 s of work when checkpointing) */
   uint64_t max_chunks;         /* stop (status SK_OK, report->complete = 0)
                                   after this many new chunks; 0 = no limit */
+  int arith;                   /* SK_ARITH_LIMBS (default) or SK_ARITH_MONTGOMERY */
 } sk_count_opts;
 
 typedef struct sk_count_report {
@@ -92,6 +103,7 @@ typedef struct sk_count_report {
   uint64_t items;              /* work items (2^{2n-1-m}) */
   int walk_bits;               /* m */
   int inner_bits;              /* unrolled Gray bits */
+  int arith;                   /* arithmetic form used */
   int block_threads, grid;
   uint64_t chunks_total, chunks_done, chunks_resumed;
   int complete;                /* 1 when every chunk is done */
@@ -121,6 +133,10 @@ int skolem_count_ex(int variant, int n, const sk_count_opts *opts, sk_u128 *out,
  * sk_count_opts.  count <= 2^20. */
 int skolem_item_residues(int variant, int n, int m, uint64_t q_lo, uint64_t count,
                          int nprimes, const uint64_t *primes, uint64_t *out);
+
+/* skolem_item_residues with a choice of arithmetic form (SK_ARITH_*). */
+int skolem_item_residues_ex(int variant, int n, int m, uint64_t q_lo, uint64_t count,
+                            int nprimes, const uint64_t *primes, int arith, uint64_t *out);
 
 /* Largest `count` accepted by skolem_item_residues_noalloc: its static device
  * scratch holds this many work items x SK_MAX_PRIMES residues (512 KiB) plus

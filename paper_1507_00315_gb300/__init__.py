@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libskolem.so")
 SKOLEM, LANGFORD, HOOKED = 0, 1, 2
 VARIANTS = {"skolem": SKOLEM, "langford": LANGFORD, "hooked": HOOKED}
 REFLECTIONS_IDENTIFIED, COUNT_ALL = 0, 1
+ARITH_LIMBS, ARITH_MONTGOMERY = 0, 1
 MAX_N = 28
 MAX_PRIMES = 4
 NOALLOC_MAX_ITEMS = 16384
@@ -47,7 +48,8 @@ class CountOpts(ctypes.Structure):
                 ("stream", ctypes.c_void_p),
                 ("checkpoint_path", ctypes.c_char_p),
                 ("chunk_items", ctypes.c_uint64),
-                ("max_chunks", ctypes.c_uint64)]
+                ("max_chunks", ctypes.c_uint64),
+                ("arith", ctypes.c_int)]
 
 
 class CountReport(ctypes.Structure):
@@ -59,6 +61,7 @@ class CountReport(ctypes.Structure):
                 ("items", ctypes.c_uint64),
                 ("walk_bits", ctypes.c_int),
                 ("inner_bits", ctypes.c_int),
+                ("arith", ctypes.c_int),
                 ("block_threads", ctypes.c_int),
                 ("grid", ctypes.c_int),
                 ("chunks_total", ctypes.c_uint64),
@@ -72,7 +75,7 @@ class CountReport(ctypes.Structure):
         k = self.nprimes
         return {"nprimes": k, "primes": list(self.primes[:k]), "residues": list(self.residues[:k]),
                 "coefficient": self.coefficient.value(), "terms": self.terms, "items": self.items,
-                "walk_bits": self.walk_bits, "inner_bits": self.inner_bits,
+                "walk_bits": self.walk_bits, "inner_bits": self.inner_bits, "arith": self.arith,
                 "block_threads": self.block_threads, "grid": self.grid,
                 "chunks_total": self.chunks_total, "chunks_done": self.chunks_done,
                 "chunks_resumed": self.chunks_resumed, "complete": bool(self.complete),
@@ -96,6 +99,10 @@ def lib():
                                            ctypes.c_uint64, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_uint64),
                                            ctypes.POINTER(ctypes.c_uint64)]
+        L.skolem_item_residues_ex.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_uint64), ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_uint64)]
         L.skolem_item_residues_noalloc.argtypes = [
             ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
             ctypes.POINTER(ctypes.c_uint64), ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]
@@ -130,7 +137,7 @@ def default_primes():
 
 
 def _opts(nprimes=0, primes=None, convention=REFLECTIONS_IDENTIFIED, walk_bits=0, block_threads=0,
-          grid=0, stream=None, checkpoint=None, chunk_items=0, max_chunks=0):
+          grid=0, stream=None, checkpoint=None, chunk_items=0, max_chunks=0, arith=ARITH_LIMBS):
     o = CountOpts()
     o.nprimes = nprimes
     for i, p in enumerate(primes or []):
@@ -143,6 +150,7 @@ def _opts(nprimes=0, primes=None, convention=REFLECTIONS_IDENTIFIED, walk_bits=0
     o.checkpoint_path = checkpoint.encode() if checkpoint else None
     o.chunk_items = chunk_items
     o.max_chunks = max_chunks
+    o.arith = arith
     return o
 
 
@@ -158,7 +166,7 @@ def count(variant, n: int) -> int:
 def count_ex(variant, n: int, **kw):
     """skolem_count_ex: returns (count or None if incomplete, report dict).
     Keywords: nprimes, primes, convention, walk_bits, block_threads, grid,
-    stream (int handle), checkpoint (path), chunk_items, max_chunks."""
+    stream (int handle), checkpoint (path), chunk_items, max_chunks, arith."""
     o = _opts(**kw)
     out = U128()
     rep = CountReport()
@@ -179,12 +187,12 @@ def int32_peak(mode: int = 0):
     return v.value, ms.value
 
 
-def item_residues(variant, n: int, m: int, q_lo: int, count_: int, primes):
-    """skolem_item_residues: list of per-item lists of residues."""
+def item_residues(variant, n: int, m: int, q_lo: int, count_: int, primes, arith=ARITH_LIMBS):
+    """skolem_item_residues(_ex): list of per-item lists of residues."""
     k = len(primes)
     P = (ctypes.c_uint64 * k)(*primes)
     out = (ctypes.c_uint64 * (count_ * k))()
-    st = lib().skolem_item_residues(_variant(variant), n, m, q_lo, count_, k, P, out)
+    st = lib().skolem_item_residues_ex(_variant(variant), n, m, q_lo, count_, k, P, arith, out)
     if st != SK_OK:
         raise SkolemError(st, "skolem_item_residues")
     return [list(out[i * k:(i + 1) * k]) for i in range(count_)]

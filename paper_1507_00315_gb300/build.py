@@ -23,6 +23,12 @@ MAX_N = 28
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
+# Extra nvcc flags (e.g. "-DSK_INNER_BITS=4" to change the unrolled Gray
+# width); objects for each flag set live in their own build directory.
+EXTRA = os.environ.get("SK_NVCC_FLAGS", "").split()
+if EXTRA:
+    import hashlib
+    BUILD = os.path.join(PKG, "_build", "x" + hashlib.sha1(" ".join(EXTRA).encode()).hexdigest()[:8])
 
 
 def _nvcc():
@@ -38,7 +44,7 @@ def _headers():
 
 
 def _sources():
-    gen = os.path.join(BUILD, "gen")
+    gen = os.path.join(PKG, "_build", "gen")
     os.makedirs(gen, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     for n in range(1, MAX_N + 1):
@@ -73,7 +79,7 @@ def build(jobs: int | None = None, verbose: bool = False) -> str:
 
     def compile_one(so):
         s, o = so
-        cmd = [nvcc] + NVCC_FLAGS + ARCH + ["-c", s, "-o", o + ".tmp"]
+        cmd = [nvcc] + NVCC_FLAGS + EXTRA + ARCH + ["-c", s, "-o", o + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {s}:\n{r.stderr}")
@@ -87,13 +93,18 @@ def build(jobs: int | None = None, verbose: bool = False) -> str:
             for s in ex.map(compile_one, todo):
                 if verbose:
                     print("compiled", os.path.basename(s), file=sys.stderr)
-    if todo or not os.path.exists(LIB):
+    stamp = os.path.join(BUILD, "linked_flags")
+    same = os.path.exists(stamp) and open(stamp).read() == " ".join(EXTRA) and \
+        os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs)
+    if todo or not same:
         cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", LIB + ".tmp"] + objs + \
               ["-Xlinker", "-rpath,/usr/local/cuda/lib64"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
         os.replace(LIB + ".tmp", LIB)
+        with open(stamp, "w") as f:
+            f.write(" ".join(EXTRA))
     return LIB
 
 

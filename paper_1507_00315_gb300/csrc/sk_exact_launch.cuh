@@ -1,4 +1,4 @@
-// sk_exact_launch.cuh -- the single-job Gray-code kernel and its launcher.
+// sk_exact_launch.cuh -- the single-job Gray-code kernels and their launchers.
 //
 // One persistent grid (a multiple of the SM count) pulls work items from a
 // device counter, one warp-sized chunk (32 items, one per lane) at a time, so
@@ -7,6 +7,12 @@
 // shuffles, and one lane per warp adds them into the job's slots with a
 // compare-and-swap modular add (order independent, so the result is
 // bit-exact whatever the schedule).
+//
+// Two arithmetic forms of the term product (same residues):
+//   limb_kernel<delta, n>       -- exact multi-limb products and sums, reduced
+//                                  modulo the primes once per work item;
+//   mont_kernel<delta, n, NPR>  -- per-term signed Montgomery products modulo
+//                                  each 62-bit prime.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -25,10 +31,11 @@ struct ExactScratch {
 struct ExactLaunch {
   ExactJob job;
   Primes P;
+  int nprimes;
   unsigned long long item_lo;            // first item of this launch
   unsigned long long item_hi;            // one past the last item
   ExactScratch* scratch;                 // device
-  unsigned long long* item_res;          // optional: [item_hi-item_lo][NPR]
+  unsigned long long* item_res;          // optional: [item_hi-item_lo][nprimes]
   int block_threads;
   int grid;                              // 0: SMs x resident blocks
   cudaStream_t stream;
@@ -37,8 +44,8 @@ struct ExactLaunch {
 constexpr int kCasLimit = 1 << 22;
 
 // Two resident 256-thread CTAs per SM: 128 registers per thread, which holds
-// the n correlations, the window of outer values and the residue
-// accumulators without spills up to n = 28.
+// the n correlations, the window of outer values and the accumulators
+// without spills.
 #ifndef SK_EXACT_MIN_BLOCKS
 #define SK_EXACT_MIN_BLOCKS 2
 #endif
@@ -56,11 +63,12 @@ __device__ __forceinline__ void atomic_addmod(unsigned long long* addr, unsigned
   atomicOr(err, 1u);
 }
 
-template <int NPR>
-__device__ __forceinline__ void warp_flush(unsigned long long (&tot)[NPR], const Primes& P,
-                                           unsigned long long* slots, unsigned int* err) {
+__device__ __forceinline__ void warp_flush(unsigned long long (&tot)[kMaxPrimes], int nprimes,
+                                           const Primes& P, unsigned long long* slots,
+                                           unsigned int* err) {
 #pragma unroll
-  for (int i = 0; i < NPR; ++i) {
+  for (int i = 0; i < kMaxPrimes; ++i) {
+    if (i >= nprimes) break;
     unsigned long long v = tot[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
@@ -70,19 +78,16 @@ __device__ __forceinline__ void warp_flush(unsigned long long (&tot)[NPR], const
   }
 }
 
-template <int DELTA, int N, int NPR>
-__global__ void __launch_bounds__(256, SK_EXACT_MIN_BLOCKS) exact_kernel(ExactJob job, Primes P,
-                                                    unsigned long long item_lo,
-                                                    unsigned long long item_hi,
-                                                    ExactScratch* scr,
-                                                    unsigned long long* item_res) {
+// The persistent work loop shared by both arithmetic forms.
+template <int DELTA, int N, class Acc>
+__device__ __forceinline__ void work_loop(const ExactJob& job, const Primes& P, int nprimes,
+                                          unsigned long long item_lo, unsigned long long item_hi,
+                                          ExactScratch* scr, unsigned long long* item_res) {
   extern __shared__ signed char sk_ws[];
   const unsigned long long count = item_hi - item_lo;
   const int lane = threadIdx.x & 31;
   signed char* ws_col = sk_ws + threadIdx.x;
-  unsigned long long tot[NPR];
-#pragma unroll
-  for (int i = 0; i < NPR; ++i) tot[i] = 0;
+  unsigned long long tot[kMaxPrimes] = {0, 0, 0, 0};
   for (;;) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(&scr->counter, 32ULL);
@@ -90,24 +95,40 @@ __global__ void __launch_bounds__(256, SK_EXACT_MIN_BLOCKS) exact_kernel(ExactJo
     if (base >= count) break;
     const unsigned long long it = base + lane;
     if (it < count) {
-      unsigned long long r[NPR];
-      run_item<DELTA, N, NPR>(job.pres, job.m, item_lo + it, P, ws_col, r);
+      unsigned long long r[kMaxPrimes];
+      Acc A(P);
+      run_item<DELTA, N>(job.pres, job.m, item_lo + it, ws_col, A, nprimes, r);
 #pragma unroll
-      for (int i = 0; i < NPR; ++i) {
+      for (int i = 0; i < kMaxPrimes; ++i) {
+        if (i >= nprimes) break;
         tot[i] = addmod(tot[i], r[i], (unsigned long long)P.pr[i].p);
-        if (item_res) item_res[it * NPR + i] = r[i];
+        if (item_res) item_res[it * nprimes + i] = r[i];
       }
     }
   }
-  warp_flush<NPR>(tot, P, scr->res, &scr->err);
+  warp_flush(tot, nprimes, P, scr->res, &scr->err);
+}
+
+template <int DELTA, int N>
+__global__ void __launch_bounds__(256, SK_EXACT_MIN_BLOCKS)
+    limb_kernel(ExactJob job, Primes P, int nprimes, unsigned long long item_lo,
+                unsigned long long item_hi, ExactScratch* scr, unsigned long long* item_res) {
+  work_loop<DELTA, N, LimbAcc<DELTA, N>>(job, P, nprimes, item_lo, item_hi, scr, item_res);
 }
 
 template <int DELTA, int N, int NPR>
-cudaError_t launch_exact(const ExactLaunch& L) {
-  static int blocks_per_sm[257] = {0};
+__global__ void __launch_bounds__(256, SK_EXACT_MIN_BLOCKS)
+    mont_kernel(ExactJob job, Primes P, unsigned long long item_lo, unsigned long long item_hi,
+                ExactScratch* scr, unsigned long long* item_res) {
+  work_loop<DELTA, N, MontAcc<DELTA, N, NPR>>(job, P, NPR, item_lo, item_hi, scr, item_res);
+}
+
+// Grid: SMs x resident CTAs per SM, never more warps than 32-item chunks.
+template <class K>
+cudaError_t exact_grid(K kernel, const ExactLaunch& L, size_t smem, int* blocks_per_sm_cache,
+                       int* grid_out) {
   static int sms = 0;
   const int bt = L.block_threads;
-  const size_t smem = (size_t)ws_len(DELTA, N) * kWsStride;
   if (bt < 32 || bt > 256 || (bt & 31)) return cudaErrorInvalidValue;
   int grid = L.grid;
   if (grid <= 0) {
@@ -116,30 +137,55 @@ cudaError_t launch_exact(const ExactLaunch& L) {
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    if (!blocks_per_sm[bt]) {
+    if (!blocks_per_sm_cache[bt]) {
       int nb = 0;
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &nb, exact_kernel<DELTA, N, NPR>, bt, smem);
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, bt, smem);
       if (e != cudaSuccess) return e;
-      blocks_per_sm[bt] = nb > 0 ? nb : 1;
+      blocks_per_sm_cache[bt] = nb > 0 ? nb : 1;
     }
-    grid = sms * blocks_per_sm[bt];
-    // never more warps than chunks of 32 items
+    grid = sms * blocks_per_sm_cache[bt];
     unsigned long long chunks = (L.item_hi - L.item_lo + 31) / 32;
     unsigned long long warps_per_block = (unsigned long long)bt / 32;
     unsigned long long need = (chunks + warps_per_block - 1) / warps_per_block;
     if ((unsigned long long)grid > need) grid = (int)(need ? need : 1);
   }
-  exact_kernel<DELTA, N, NPR><<<grid, bt, smem, L.stream>>>(L.job, L.P, L.item_lo, L.item_hi,
-                                                         L.scratch, L.item_res);
+  *grid_out = grid;
+  return cudaSuccess;
+}
+
+template <int DELTA, int N, int NPR>
+cudaError_t launch_exact(const ExactLaunch& L) {
+  static int bps[257] = {0};
+  if (L.nprimes != NPR) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)ws_len(DELTA, N) * kWsStride;
+  int grid = 0;
+  cudaError_t e = exact_grid(mont_kernel<DELTA, N, NPR>, L, smem, bps, &grid);
+  if (e != cudaSuccess) return e;
+  mont_kernel<DELTA, N, NPR><<<grid, L.block_threads, smem, L.stream>>>(
+      L.job, L.P, L.item_lo, L.item_hi, L.scratch, L.item_res);
+  return cudaGetLastError();
+}
+
+template <int DELTA, int N>
+cudaError_t launch_limb(const ExactLaunch& L) {
+  static int bps[257] = {0};
+  if (L.nprimes < 1 || L.nprimes > kMaxPrimes) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)ws_len(DELTA, N) * kWsStride;
+  int grid = 0;
+  cudaError_t e = exact_grid(limb_kernel<DELTA, N>, L, smem, bps, &grid);
+  if (e != cudaSuccess) return e;
+  limb_kernel<DELTA, N><<<grid, L.block_threads, smem, L.stream>>>(
+      L.job, L.P, L.nprimes, L.item_lo, L.item_hi, L.scratch, L.item_res);
   return cudaGetLastError();
 }
 
 typedef cudaError_t (*ExactLaunchFn)(const ExactLaunch&);
 
-// Launchers for delta in {0, 1}, n in [1, kMaxN], primes in {3, 4}
-// (null for combinations that were not compiled).
+// Montgomery-form launchers for delta in {0, 1}, n in [1, kMaxN], primes in
+// {3, 4} (null for combinations that were not compiled).
 ExactLaunchFn exact_launcher(int delta, int n, int nprimes);
+// Exact-limb launchers for delta in {0, 1}, n in [1, kMaxN].
+ExactLaunchFn limb_launcher(int delta, int n);
 
 }  // namespace sk
 
@@ -147,4 +193,6 @@ ExactLaunchFn exact_launcher(int delta, int n, int nprimes);
   template cudaError_t sk::launch_exact<0, N, 3>(const sk::ExactLaunch&);      \
   template cudaError_t sk::launch_exact<0, N, 4>(const sk::ExactLaunch&);      \
   template cudaError_t sk::launch_exact<1, N, 3>(const sk::ExactLaunch&);      \
-  template cudaError_t sk::launch_exact<1, N, 4>(const sk::ExactLaunch&);
+  template cudaError_t sk::launch_exact<1, N, 4>(const sk::ExactLaunch&);      \
+  template cudaError_t sk::launch_limb<0, N>(const sk::ExactLaunch&);          \
+  template cudaError_t sk::launch_limb<1, N>(const sk::ExactLaunch&);

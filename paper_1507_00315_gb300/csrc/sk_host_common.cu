@@ -17,7 +17,8 @@ int prepare_primes(const sk_count_opts* o, int* nprimes, uint64_t* primes, Prime
   if (k < 3 || k > SK_MAX_PRIMES) return SK_EINVAL;
   for (int i = 0; i < k; ++i) {
     uint64_t p = (o && o->primes[i]) ? o->primes[i] : kDefaultPrimes[i];
-    if (!(p & 1) || p <= (1ULL << 40) || p >= (1ULL << 62)) return SK_EINVAL;
+    // the device's Montgomery step relies on a high limb of exactly 2^30
+    if (!(p & 1) || p <= (1ULL << 62) - (1ULL << 31) || p >= (1ULL << 62)) return SK_EINVAL;
     for (int j = 0; j < i; ++j)
       if (gcd_u64(p, primes[j]) != 1) return SK_EINVAL;
     primes[i] = p;

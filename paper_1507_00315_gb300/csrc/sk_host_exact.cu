@@ -31,6 +31,18 @@ SK_EXTERN_EXACT(23) SK_EXTERN_EXACT(24) SK_EXTERN_EXACT(25) SK_EXTERN_EXACT(26)
 SK_EXTERN_EXACT(27) SK_EXTERN_EXACT(28)
 #undef SK_EXTERN_EXACT
 
+#define SK_EXTERN_LIMB(N)                                                          \
+  extern template cudaError_t launch_limb<0, N>(const ExactLaunch&);                \
+  extern template cudaError_t launch_limb<1, N>(const ExactLaunch&);
+SK_EXTERN_LIMB(1) SK_EXTERN_LIMB(2) SK_EXTERN_LIMB(3) SK_EXTERN_LIMB(4) SK_EXTERN_LIMB(5)
+SK_EXTERN_LIMB(6) SK_EXTERN_LIMB(7) SK_EXTERN_LIMB(8) SK_EXTERN_LIMB(9) SK_EXTERN_LIMB(10)
+SK_EXTERN_LIMB(11) SK_EXTERN_LIMB(12) SK_EXTERN_LIMB(13) SK_EXTERN_LIMB(14)
+SK_EXTERN_LIMB(15) SK_EXTERN_LIMB(16) SK_EXTERN_LIMB(17) SK_EXTERN_LIMB(18)
+SK_EXTERN_LIMB(19) SK_EXTERN_LIMB(20) SK_EXTERN_LIMB(21) SK_EXTERN_LIMB(22)
+SK_EXTERN_LIMB(23) SK_EXTERN_LIMB(24) SK_EXTERN_LIMB(25) SK_EXTERN_LIMB(26)
+SK_EXTERN_LIMB(27) SK_EXTERN_LIMB(28)
+#undef SK_EXTERN_LIMB
+
 #define SK_ROW(N) {{launch_exact<0, N, 3>, launch_exact<0, N, 4>}, {launch_exact<1, N, 3>, launch_exact<1, N, 4>}}
 static const ExactLaunchFn kTable[kMaxN + 1][2][2] = {
     {{nullptr, nullptr}, {nullptr, nullptr}},
@@ -44,6 +56,31 @@ ExactLaunchFn exact_launcher(int delta, int n, int nprimes) {
   if (delta < 0 || delta > 1 || n < 1 || n > kMaxN || nprimes < 3 || nprimes > 4) return nullptr;
   return kTable[n][delta][nprimes - 3];
 }
+
+#define SK_LROW(N) {launch_limb<0, N>, launch_limb<1, N>}
+static const ExactLaunchFn kLimbTable[kMaxN + 1][2] = {
+    {nullptr, nullptr},
+    SK_LROW(1), SK_LROW(2), SK_LROW(3), SK_LROW(4), SK_LROW(5), SK_LROW(6), SK_LROW(7),
+    SK_LROW(8), SK_LROW(9), SK_LROW(10), SK_LROW(11), SK_LROW(12), SK_LROW(13), SK_LROW(14),
+    SK_LROW(15), SK_LROW(16), SK_LROW(17), SK_LROW(18), SK_LROW(19), SK_LROW(20), SK_LROW(21),
+    SK_LROW(22), SK_LROW(23), SK_LROW(24), SK_LROW(25), SK_LROW(26), SK_LROW(27), SK_LROW(28)};
+#undef SK_LROW
+
+ExactLaunchFn limb_launcher(int delta, int n) {
+  if (delta < 0 || delta > 1 || n < 1 || n > kMaxN) return nullptr;
+  return kLimbTable[n][delta];
+}
+
+// Largest walk width of the exact-limb form (compile-time table per (delta, n)).
+template <int D, int N>
+struct LimbMaxM { static constexpr int v = limb_max_walk_bits(D, N); };
+#define SK_LM(N) {LimbMaxM<0, N>::v, LimbMaxM<1, N>::v}
+static const int kLimbMaxM[kMaxN + 1][2] = {
+    {0, 0}, SK_LM(1), SK_LM(2), SK_LM(3), SK_LM(4), SK_LM(5), SK_LM(6), SK_LM(7), SK_LM(8),
+    SK_LM(9), SK_LM(10), SK_LM(11), SK_LM(12), SK_LM(13), SK_LM(14), SK_LM(15), SK_LM(16),
+    SK_LM(17), SK_LM(18), SK_LM(19), SK_LM(20), SK_LM(21), SK_LM(22), SK_LM(23), SK_LM(24),
+    SK_LM(25), SK_LM(26), SK_LM(27), SK_LM(28)};
+#undef SK_LM
 
 // ------------------------------------------------------------ planning
 
@@ -69,7 +106,7 @@ int default_walk_bits(int n) {
 }
 
 struct Plan {
-  int variant, n, delta, m, U, nprimes, block_threads, grid;
+  int variant, n, delta, m, U, nprimes, block_threads, grid, arith;
   unsigned long long pres, items;
   uint64_t primes[kMaxPrimes];
   Primes P;
@@ -85,22 +122,32 @@ static int make_plan(int variant, int n, const sk_count_opts* o, Plan* pl) {
   int st = prepare_primes(o, &pl->nprimes, pl->primes, &pl->P);
   if (st) return st;
   const int F = 2 * n - 1;
+  pl->arith = o ? o->arith : SK_ARITH_LIMBS;
+  if (pl->arith != SK_ARITH_LIMBS && pl->arith != SK_ARITH_MONTGOMERY) return SK_EINVAL;
   pl->U = inner_bits(n);
-  pl->m = (o && o->walk_bits) ? o->walk_bits : default_walk_bits(n);
-  if (pl->m < pl->U || pl->m > F || F - pl->m > 40) return SK_EINVAL;
+  const int mmax = pl->arith == SK_ARITH_LIMBS ? kLimbMaxM[n][pl->delta] : F;
+  if (o && o->walk_bits) {
+    pl->m = o->walk_bits;
+  } else {
+    pl->m = default_walk_bits(n);
+    if (pl->m > mmax) pl->m = mmax;
+  }
+  if (pl->m < pl->U || pl->m > F || pl->m > mmax || F - pl->m > 56) return SK_EINVAL;
   pl->items = 1ULL << (F - pl->m);
   pl->pres = position_mask(variant, n);
   pl->block_threads = (o && o->block_threads) ? o->block_threads : 256;
   if (pl->block_threads < 32 || pl->block_threads > 256 || (pl->block_threads & 31)) return SK_EINVAL;
   pl->grid = (o && o->grid > 0) ? o->grid : 0;
-  pl->fn = exact_launcher(pl->delta, n, pl->nprimes);
+  pl->fn = pl->arith == SK_ARITH_LIMBS ? limb_launcher(pl->delta, n)
+                                       : exact_launcher(pl->delta, n, pl->nprimes);
   if (!pl->fn) return SK_EINVAL;
   return SK_OK;
 }
 
-// Multiplies raw residues by R^{e}, e = groups - 2, removing the Montgomery
-// factor every term carries.
+// Multiplies raw residues of the Montgomery form by R^{e}, e = groups - 2,
+// removing the factor every term carries (the limb form has none).
 static void unmont(const Plan& pl, uint64_t* res) {
+  if (pl.arith != SK_ARITH_MONTGOMERY) return;
   GroupInfo gi = make_groups(pl.delta, pl.n);
   int e = gi.g > 2 ? gi.g - 2 : 0;
   for (int i = 0; i < pl.nprimes; ++i) {
@@ -122,6 +169,7 @@ static int run_chunk(const Plan& pl, unsigned long long lo, unsigned long long h
   L.job.m = pl.m;
   L.job.job = 0;
   L.P = pl.P;
+  L.nprimes = pl.nprimes;
   L.item_lo = lo;
   L.item_hi = hi;
   L.scratch = dscr;
@@ -159,6 +207,7 @@ struct Ckpt {
 static std::string ckpt_header(const Plan& pl, unsigned long long chunk_items,
                                unsigned long long nchunks) {
   char buf[512];
+  // the arithmetic form is not part of the job: both give the same residues
   std::snprintf(buf, sizeof(buf), "SKCKPT1 v=%d n=%d m=%d k=%d p=%llu,%llu,%llu,%llu items=%llu chunk=%llu chunks=%llu",
                 pl.variant, pl.n, pl.m, pl.nprimes, (unsigned long long)pl.primes[0],
                 (unsigned long long)pl.primes[1], (unsigned long long)pl.primes[2],
@@ -338,6 +387,7 @@ int count_impl(int variant, int n, const sk_count_opts* o, sk_u128* out, sk_coun
     rep->items = pl.items;
     rep->walk_bits = pl.m;
     rep->inner_bits = pl.U;
+    rep->arith = pl.arith;
     rep->block_threads = pl.block_threads;
     rep->grid = pl.grid;
     rep->chunks_total = nchunks;
@@ -365,11 +415,12 @@ int count_impl(int variant, int n, const sk_count_opts* o, sk_u128* out, sk_coun
 }
 
 int item_residues_impl(int variant, int n, int m, uint64_t q_lo, uint64_t count, int nprimes,
-                       const uint64_t* primes, uint64_t* out) {
+                       const uint64_t* primes, int arith, uint64_t* out) {
   if (!out || !primes || count == 0 || count > (1ULL << 20)) return SK_EINVAL;
   sk_count_opts o;
   std::memset(&o, 0, sizeof(o));
   o.nprimes = nprimes;
+  o.arith = arith;
   for (int i = 0; i < nprimes && i < SK_MAX_PRIMES; ++i) o.primes[i] = primes[i];
   o.walk_bits = m;
   Plan pl;
@@ -427,5 +478,11 @@ extern "C" int skolem_count_ex(int variant, int n, const sk_count_opts* opts, sk
 
 extern "C" int skolem_item_residues(int variant, int n, int m, uint64_t q_lo, uint64_t count,
                                     int nprimes, const uint64_t* primes, uint64_t* out) {
-  return sk::item_residues_impl(variant, n, m, q_lo, count, nprimes, primes, out);
+  return sk::item_residues_impl(variant, n, m, q_lo, count, nprimes, primes, SK_ARITH_LIMBS, out);
+}
+
+extern "C" int skolem_item_residues_ex(int variant, int n, int m, uint64_t q_lo, uint64_t count,
+                                       int nprimes, const uint64_t* primes, int arith,
+                                       uint64_t* out) {
+  return sk::item_residues_impl(variant, n, m, q_lo, count, nprimes, primes, arith, out);
 }

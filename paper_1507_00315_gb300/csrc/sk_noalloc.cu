@@ -103,6 +103,7 @@ extern "C" int skolem_item_residues_noalloc(int variant, int n, int m, uint64_t 
   L.job.m = m;
   L.job.job = 0;
   L.P = P;
+  L.nprimes = k;
   L.item_lo = q_lo;
   L.item_hi = q_lo + count;
   L.scratch = rec;

@@ -14,21 +14,26 @@ pytestmark = pytest.mark.gpu
 SK, LA, HO = 0, 1, 2
 
 
+ARITHS = [sk.ARITH_LIMBS, sk.ARITH_MONTGOMERY]
+
+
+@pytest.mark.parametrize("arith", ARITHS)
 @pytest.mark.parametrize("variant", [SK, LA, HO])
-def test_small_orders_bit_exact_vs_backtracking(variant):
+def test_small_orders_bit_exact_vs_backtracking(variant, arith):
     # Plain exact counts n = 1..12 (Skolem 4..12 and Langford 3..12 included).
     for n in range(1, 13):
-        got, rep = sk.count_ex(variant, n, convention=sk.COUNT_ALL)
+        got, rep = sk.count_ex(variant, n, convention=sk.COUNT_ALL, arith=arith)
         want = oracle.backtrack_count(variant, n) if n <= 10 else oracle.coefficient(variant, n, threads=8)
         assert got == want, (variant, n, got, want)
         assert rep["complete"] and rep["terms"] == 1 << (2 * n - 1)
 
 
+@pytest.mark.parametrize("arith", ARITHS)
 @pytest.mark.parametrize("variant", [SK, LA, HO])
-def test_residues_equal_oracle_sum(variant):
+def test_residues_equal_oracle_sum(variant, arith):
     # H mod p of the whole half sum equals Algorithm 1's exact sum mod p.
     for n in (5, 9, 11):
-        _, rep = sk.count_ex(variant, n, nprimes=4)
+        _, rep = sk.count_ex(variant, n, nprimes=4, arith=arith)
         H = oracle.signed_sum(variant, n, half=True, threads=8)
         for p, r in zip(rep["primes"], rep["residues"]):
             assert r == H % p
@@ -65,11 +70,16 @@ def test_mid_size_against_paper(variant, n, skolem_table, langford_table):
     assert rep["complete"]
 
 
+def test_mid_size_montgomery_form(skolem_table):
+    assert sk.count_ex(SK, 20, arith=sk.ARITH_MONTGOMERY)[0] == skolem_table[20]
+
+
+@pytest.mark.parametrize("arith", ARITHS)
 @pytest.mark.parametrize("variant,n", [(SK, 16), (LA, 19), (HO, 18), (SK, 20)])
-def test_sampled_items_at_full_size(variant, n):
+def test_sampled_items_at_full_size(variant, n, arith):
     # The full-size launch's own walk width; a few items recomputed by the
     # oracle one by one (first, last, random).
-    _, rep = sk.count_ex(variant, n)
+    _, rep = sk.count_ex(variant, n, arith=arith)
     m, items = rep["walk_bits"], rep["items"]
     if m > 18:
         pytest.skip("items too large for the oracle")
@@ -77,7 +87,7 @@ def test_sampled_items_at_full_size(variant, n):
     rng = random.Random(n)
     qs = sorted({0, items - 1, rng.randrange(items), rng.randrange(items)})
     for q in qs:
-        got = sk.item_residues(variant, n, m, q, 1, primes)[0]
+        got = sk.item_residues(variant, n, m, q, 1, primes, arith=arith)[0]
         want = [oracle.partial_sum_mod(variant, n, m, q, p) for p in primes]
         assert got == want, (q, got, want)
 
@@ -87,23 +97,39 @@ def test_item_residues_ragged_tiles(variant):
     # many items per launch, a count that is not a multiple of 32 (ragged
     # last warp), several inner tiles per item
     n, m = 7, 7
-    primes = [(1 << 61) - 1, 4611686018427387847, 4611686018427387817]
+    primes = [4611686017353646079, 4611686018427387847, 4611686018427387817]
     got = sk.item_residues(variant, n, m, 3, 61, primes)
     for i, q in enumerate(range(3, 64)):
         for j, p in enumerate(primes):
             assert got[i][j] == oracle.partial_sum_mod(variant, n, m, q, p)
 
 
+@pytest.mark.parametrize("variant,n,m", [(SK, 24, 9), (LA, 24, 9), (HO, 26, 8), (SK, 28, 7),
+                                         (LA, 28, 7), (HO, 21, 10)])
+def test_large_orders_items_both_forms(variant, n, m):
+    # the widest limb accumulators and the longest Montgomery chains, on
+    # items small enough for the oracle (prefixes spread over the range)
+    primes = sk.default_primes()[:4]
+    F = 2 * n - 1
+    for q in (0, (1 << (F - m)) - 1, 0x5A5A5A5A5A5 % (1 << (F - m))):
+        a = sk.item_residues(variant, n, m, q, 1, primes, arith=sk.ARITH_LIMBS)[0]
+        b = sk.item_residues(variant, n, m, q, 1, primes, arith=sk.ARITH_MONTGOMERY)[0]
+        want = [oracle.partial_sum_mod(variant, n, m, q, p) for p in primes]
+        assert a == want and b == want, (q, a, b, want)
+
+
 def test_schedule_independence():
     # walk width, block size and grid change the schedule, not the residues
     base = sk.count_ex(SK, 13, nprimes=4)[1]["residues"]
     for kw in ({"walk_bits": 6}, {"walk_bits": 25}, {"block_threads": 64}, {"grid": 3},
-               {"walk_bits": 9, "block_threads": 96, "grid": 7}):
+               {"walk_bits": 9, "block_threads": 96, "grid": 7}, {"arith": sk.ARITH_MONTGOMERY},
+               {"arith": sk.ARITH_MONTGOMERY, "walk_bits": 20, "block_threads": 128}):
         assert sk.count_ex(SK, 13, nprimes=4, **kw)[1]["residues"] == base, kw
 
 
 def test_custom_primes_and_check_prime():
-    primes = [4611686018427387751, 4611686018427387737, (1 << 61) - 1, 2305843009213693921]
+    # other primes of the accepted window (2^62 - 2^31, 2^62)
+    primes = [4611686018427387751, 4611686018427387737, 4611686017353646079, 4611686016279916631]
     c, rep = sk.count_ex(LA, 12, nprimes=4, primes=primes)
     assert c == 108144
     assert rep["primes"] == primes
@@ -116,6 +142,8 @@ def test_invalid_arguments():
         assert e.value.status == sk.SK_EINVAL
     with pytest.raises(sk.SkolemError):
         sk.count_ex(SK, 8, primes=[4, 0, 0])
+    with pytest.raises(sk.SkolemError):          # below the moduli window
+        sk.count_ex(SK, 8, primes=[(1 << 61) - 1, 0, 0])
     with pytest.raises(sk.SkolemError):
         sk.count_ex(SK, 8, block_threads=100)
 
