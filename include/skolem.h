@@ -63,7 +63,8 @@ enum { SK_COUNT_REFLECTIONS_IDENTIFIED = 0, SK_COUNT_ALL = 1 };
  * (|prod c_k| <= prod_k L_k, L_k = number of pairs at distance d_k) and added
  * into an exact accumulator; each work item's sum is reduced modulo the
  * primes once.  SK_ARITH_MONTGOMERY: every term's product is formed modulo
- * each prime by signed Montgomery steps (R = 2^32). */
+ * each prime by signed Montgomery steps (R = 2^32); compiled for three
+ * moduli only (nprimes = 3). */
 enum { SK_ARITH_LIMBS = 0, SK_ARITH_MONTGOMERY = 1 };
 #define SK_MAX_PRIMES 4
 
@@ -123,6 +124,68 @@ int skolem_count(int variant, int n, sk_u128 *out);
  * (opts->max_chunks) and resume later; out is written only when complete. */
 int skolem_count_ex(int variant, int n, const sk_count_opts *opts, sk_u128 *out,
                     sk_count_report *rep);
+
+/* ------------------------------------------------------------ batches */
+
+typedef struct sk_job { int variant; int n; } sk_job;
+
+/* SK_BATCH_PERSISTENT: every job in one persistent launch (captured in a CUDA
+ * graph unless no_graph) pulling 32-item chunks from a device queue, largest
+ * job first.  SK_BATCH_PER_JOB: one launch per job, back to back on the
+ * stream (the baseline). */
+enum { SK_BATCH_PERSISTENT = 0, SK_BATCH_PER_JOB = 1 };
+
+typedef struct sk_batch_opts {
+  int nprimes;                    /* 0 -> 3; as in sk_count_opts */
+  uint64_t primes[SK_MAX_PRIMES]; /* 0 -> built-in */
+  int convention;                 /* SK_COUNT_* for every job */
+  int mode;                       /* SK_BATCH_PERSISTENT (default) or SK_BATCH_PER_JOB */
+  int no_graph;                   /* persistent mode: 0 (default) captures the
+                                     launch in a CUDA graph and replays it;
+                                     1 launches it directly */
+  int repeats;                    /* runs of the whole batch (>= 1; 0 -> 1); the
+                                     report gives the last and the fastest */
+  int autotune;                   /* 1: tune walk width (and block size) per
+                                     (variant, n) before the run, untimed */
+  int block_threads;              /* 0 -> 256 or the tuned value */
+  int walk_bits[SK_MAX_N + 1];    /* per n; 0 -> tuned or planner default */
+  void *stream;                   /* cudaStream_t or NULL */
+} sk_batch_opts;
+
+typedef struct sk_batch_report {
+  double kernel_ms;               /* device time of the last repeat */
+  double kernel_ms_min;           /* fastest repeat */
+  double wall_ms;                 /* host time of the whole call */
+  double prepare_ms;              /* planning, tuning, graph capture */
+  uint64_t terms;                 /* sum over jobs of 2^{2n-1} */
+  uint64_t chunks;                /* 32-item chunks of the queue */
+  int launches;                   /* kernel launches per repeat */
+  int grid, block_threads;
+} sk_batch_report;
+
+/* Exact counts of njobs jobs (host array; 1 <= njobs <= 4096; each job as in
+ * skolem_count).  outs (host, njobs): the counts in opts->convention;
+ * status (host, njobs, may be NULL): per-job SK status (a job whose CRT checks
+ * fail gets SK_EMISMATCH; the call then returns SK_EMISMATCH too).  opts and
+ * rep may be NULL.  The persistent mode is an engineering addition (the paper
+ * runs one job per GPU launch, Sec. 2.2). */
+int skolem_count_batch(const sk_job *jobs, int njobs, const sk_batch_opts *opts, sk_u128 *outs,
+                       int *status, sk_batch_report *rep);
+
+typedef struct sk_tune_result {
+  int walk_bits;                  /* fastest m */
+  int block_threads;              /* fastest block size */
+  double terms_per_s;             /* its rate on the sample */
+  int candidates;                 /* configurations timed */
+} sk_tune_result;
+
+/* Times candidate walk widths m (planner default and +-2, +-4, within the
+ * valid range) and block sizes (128, 256) of the exact-limb kernel for one
+ * (variant, n) on the first work items (2^33 terms at most) and returns the
+ * fastest.  The result is also cached in the library and used by
+ * skolem_count_batch when opts->autotune is set.  opts may be NULL (only
+ * nprimes/primes/stream are read). */
+int skolem_autotune(int variant, int n, const sk_batch_opts *opts, sk_tune_result *out);
 
 /* Residues of single work items, for sampled checks at full size.  Item q of
  * walk width m fixes the free variables m..2n-2 (bit b of q set means

@@ -82,6 +82,45 @@ class CountReport(ctypes.Structure):
                 "kernel_ms": self.kernel_ms, "wall_ms": self.wall_ms}
 
 
+class Job(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("n", ctypes.c_int)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("nprimes", ctypes.c_int),
+                ("primes", ctypes.c_uint64 * MAX_PRIMES),
+                ("convention", ctypes.c_int),
+                ("mode", ctypes.c_int),
+                ("no_graph", ctypes.c_int),
+                ("repeats", ctypes.c_int),
+                ("autotune", ctypes.c_int),
+                ("block_threads", ctypes.c_int),
+                ("walk_bits", ctypes.c_int * (MAX_N + 1)),
+                ("stream", ctypes.c_void_p)]
+
+
+class BatchReport(ctypes.Structure):
+    _fields_ = [("kernel_ms", ctypes.c_double),
+                ("kernel_ms_min", ctypes.c_double),
+                ("wall_ms", ctypes.c_double),
+                ("prepare_ms", ctypes.c_double),
+                ("terms", ctypes.c_uint64),
+                ("chunks", ctypes.c_uint64),
+                ("launches", ctypes.c_int),
+                ("grid", ctypes.c_int),
+                ("block_threads", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("walk_bits", ctypes.c_int), ("block_threads", ctypes.c_int),
+                ("terms_per_s", ctypes.c_double), ("candidates", ctypes.c_int)]
+
+
+BATCH_PERSISTENT, BATCH_PER_JOB = 0, 1
+
 _lib = None
 
 
@@ -106,6 +145,11 @@ def lib():
         L.skolem_item_residues_noalloc.argtypes = [
             ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
             ctypes.POINTER(ctypes.c_uint64), ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]
+        L.skolem_count_batch.argtypes = [ctypes.POINTER(Job), ctypes.c_int, ctypes.POINTER(BatchOpts),
+                                         ctypes.POINTER(U128), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(BatchReport)]
+        L.skolem_autotune.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(BatchOpts),
+                                      ctypes.POINTER(TuneResult)]
         L.sk_int32_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double)]
         L.sk_default_primes.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
@@ -209,3 +253,48 @@ def item_residues_noalloc(variant, n: int, m: int, q_lo: int, count_: int, prime
     if st != SK_OK:
         raise SkolemError(st, "skolem_item_residues_noalloc")
     return [list(out[i * k:(i + 1) * k]) for i in range(count_)]
+
+
+def _batch_opts(nprimes=0, primes=None, convention=REFLECTIONS_IDENTIFIED, mode=BATCH_PERSISTENT,
+                no_graph=False, repeats=1, autotune=False, block_threads=0, walk_bits=None,
+                stream=None):
+    o = BatchOpts()
+    o.nprimes = nprimes
+    for i, p in enumerate(primes or []):
+        o.primes[i] = p
+    o.convention = convention
+    o.mode = mode
+    o.no_graph = int(bool(no_graph))
+    o.repeats = repeats
+    o.autotune = int(bool(autotune))
+    o.block_threads = block_threads
+    for n, m in (walk_bits or {}).items():
+        o.walk_bits[n] = m
+    o.stream = stream
+    return o
+
+
+def count_batch(jobs, **kw):
+    """skolem_count_batch: jobs = [(variant, n), ...].  Returns (counts,
+    statuses, report dict).  Keywords: nprimes, primes, convention, mode
+    (BATCH_PERSISTENT / BATCH_PER_JOB), no_graph, repeats, autotune,
+    block_threads, walk_bits ({n: m}), stream."""
+    J = (Job * len(jobs))(*[Job(_variant(v), n) for v, n in jobs])
+    o = _batch_opts(**kw)
+    outs = (U128 * len(jobs))()
+    stat = (ctypes.c_int * len(jobs))()
+    rep = BatchReport()
+    st = lib().skolem_count_batch(J, len(jobs), ctypes.byref(o), outs, stat, ctypes.byref(rep))
+    if st != SK_OK:
+        raise SkolemError(st, "skolem_count_batch")
+    return [o_.value() for o_ in outs], list(stat), rep.as_dict()
+
+
+def autotune(variant, n: int, **kw):
+    """skolem_autotune: dict(walk_bits, block_threads, terms_per_s, candidates)."""
+    o = _batch_opts(**kw)
+    r = TuneResult()
+    st = lib().skolem_autotune(_variant(variant), n, ctypes.byref(o), ctypes.byref(r))
+    if st != SK_OK:
+        raise SkolemError(st, "skolem_autotune")
+    return {k: getattr(r, k) for k, _ in r._fields_}

@@ -22,7 +22,11 @@ LIB = os.path.join(PKG, "libskolem.so")
 MAX_N = 28
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
+# Relocatable device code: the batch kernel calls the per-n walk functions
+# across translation units (resolved by the device-link step below); every
+# function is held to 128 registers, the budget of the kernels that call them.
+NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-rdc=true", "-maxrregcount=128",
+              "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]
 # Extra nvcc flags (e.g. "-DSK_INNER_BITS=4" to change the unrolled Gray
 # width); objects for each flag set live in their own build directory.
 EXTRA = os.environ.get("SK_NVCC_FLAGS", "").split()
@@ -49,7 +53,8 @@ def _sources():
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     for n in range(1, MAX_N + 1):
         p = os.path.join(gen, f"sk_exact_n{n:02d}.cu")
-        text = f'#include "sk_exact_launch.cuh"\nSK_INSTANTIATE_EXACT({n})\n'
+        text = (f'#include "sk_exact_launch.cuh"\n#include "sk_batch.cuh"\n'
+                f'SK_INSTANTIATE_EXACT({n})\nSK_DEFINE_BATCH({n})\n')
         if not os.path.exists(p) or open(p).read() != text:
             with open(p, "w") as f:
                 f.write(text)
@@ -97,8 +102,13 @@ def build(jobs: int | None = None, verbose: bool = False) -> str:
     same = os.path.exists(stamp) and open(stamp).read() == " ".join(EXTRA) and \
         os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs)
     if todo or not same:
+        dlink = os.path.join(BUILD, "sk_dlink.o")
+        cmd = [nvcc] + ARCH + ["-dlink", "-Xcompiler", "-fPIC", "-o", dlink] + objs
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"device link failed:\n{r.stderr}")
         cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", LIB + ".tmp"] + objs + \
-              ["-Xlinker", "-rpath,/usr/local/cuda/lib64"]
+              [dlink, "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -51,6 +51,10 @@ struct Primes {
   Prime pr[kMaxPrimes];
 };
 
+struct Res4 {                    // residues of one work item
+  unsigned long long r[kMaxPrimes];
+};
+
 // Parameters of one exact-count problem as the kernels see it.
 struct ExactJob {
   unsigned long long pres;   // bit i set iff position i+1 belongs to P

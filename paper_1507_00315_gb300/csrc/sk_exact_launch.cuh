@@ -78,8 +78,44 @@ __device__ __forceinline__ void warp_flush(unsigned long long (&tot)[kMaxPrimes]
   }
 }
 
+// One exact-limb work item, compiled once per (delta, n) and called by both
+// the single-job kernel and the batch kernel.
+template <int DELTA, int N>
+__device__ __noinline__ Res4 limb_item(unsigned long long pres, int m, unsigned long long item,
+                                       const Primes* P, int nprimes, signed char* ws_col) {
+  LimbAcc<DELTA, N> A(*P);
+  unsigned long long r[kMaxPrimes];
+  run_item<DELTA, N>(pres, m, item, ws_col, A, nprimes, r);
+  Res4 out;
+#pragma unroll
+  for (int i = 0; i < kMaxPrimes; ++i) out.r[i] = r[i];
+  return out;
+}
+
+template <int DELTA, int N>
+struct LimbItem {
+  __device__ __forceinline__ static Res4 eval(const ExactJob& job, const Primes& P, int nprimes,
+                                              unsigned long long item, signed char* ws_col) {
+    return limb_item<DELTA, N>(job.pres, job.m, item, &P, nprimes, ws_col);
+  }
+};
+
+template <int DELTA, int N, int NPR>
+struct MontItem {
+  __device__ __forceinline__ static Res4 eval(const ExactJob& job, const Primes& P, int nprimes,
+                                              unsigned long long item, signed char* ws_col) {
+    MontAcc<DELTA, N, NPR> A(P);
+    unsigned long long r[kMaxPrimes];
+    run_item<DELTA, N>(job.pres, job.m, item, ws_col, A, nprimes, r);
+    Res4 out;
+#pragma unroll
+    for (int i = 0; i < kMaxPrimes; ++i) out.r[i] = r[i];
+    return out;
+  }
+};
+
 // The persistent work loop shared by both arithmetic forms.
-template <int DELTA, int N, class Acc>
+template <class Item>
 __device__ __forceinline__ void work_loop(const ExactJob& job, const Primes& P, int nprimes,
                                           unsigned long long item_lo, unsigned long long item_hi,
                                           ExactScratch* scr, unsigned long long* item_res) {
@@ -95,14 +131,12 @@ __device__ __forceinline__ void work_loop(const ExactJob& job, const Primes& P, 
     if (base >= count) break;
     const unsigned long long it = base + lane;
     if (it < count) {
-      unsigned long long r[kMaxPrimes];
-      Acc A(P);
-      run_item<DELTA, N>(job.pres, job.m, item_lo + it, ws_col, A, nprimes, r);
+      const Res4 r = Item::eval(job, P, nprimes, item_lo + it, ws_col);
 #pragma unroll
       for (int i = 0; i < kMaxPrimes; ++i) {
         if (i >= nprimes) break;
-        tot[i] = addmod(tot[i], r[i], (unsigned long long)P.pr[i].p);
-        if (item_res) item_res[it * nprimes + i] = r[i];
+        tot[i] = addmod(tot[i], r.r[i], (unsigned long long)P.pr[i].p);
+        if (item_res) item_res[it * nprimes + i] = r.r[i];
       }
     }
   }
@@ -113,14 +147,14 @@ template <int DELTA, int N>
 __global__ void __launch_bounds__(256, SK_EXACT_MIN_BLOCKS)
     limb_kernel(ExactJob job, Primes P, int nprimes, unsigned long long item_lo,
                 unsigned long long item_hi, ExactScratch* scr, unsigned long long* item_res) {
-  work_loop<DELTA, N, LimbAcc<DELTA, N>>(job, P, nprimes, item_lo, item_hi, scr, item_res);
+  work_loop<LimbItem<DELTA, N>>(job, P, nprimes, item_lo, item_hi, scr, item_res);
 }
 
 template <int DELTA, int N, int NPR>
 __global__ void __launch_bounds__(256, SK_EXACT_MIN_BLOCKS)
     mont_kernel(ExactJob job, Primes P, unsigned long long item_lo, unsigned long long item_hi,
                 ExactScratch* scr, unsigned long long* item_res) {
-  work_loop<DELTA, N, MontAcc<DELTA, N, NPR>>(job, P, NPR, item_lo, item_hi, scr, item_res);
+  work_loop<MontItem<DELTA, N, NPR>>(job, P, NPR, item_lo, item_hi, scr, item_res);
 }
 
 // Grid: SMs x resident CTAs per SM, never more warps than 32-item chunks.
@@ -181,8 +215,9 @@ cudaError_t launch_limb(const ExactLaunch& L) {
 
 typedef cudaError_t (*ExactLaunchFn)(const ExactLaunch&);
 
-// Montgomery-form launchers for delta in {0, 1}, n in [1, kMaxN], primes in
-// {3, 4} (null for combinations that were not compiled).
+// Montgomery-form launchers for delta in {0, 1}, n in [1, kMaxN], three
+// primes (null for combinations that were not compiled; four moduli go
+// through the exact-limb form).
 ExactLaunchFn exact_launcher(int delta, int n, int nprimes);
 // Exact-limb launchers for delta in {0, 1}, n in [1, kMaxN].
 ExactLaunchFn limb_launcher(int delta, int n);
@@ -191,8 +226,6 @@ ExactLaunchFn limb_launcher(int delta, int n);
 
 #define SK_INSTANTIATE_EXACT(N)                                                \
   template cudaError_t sk::launch_exact<0, N, 3>(const sk::ExactLaunch&);      \
-  template cudaError_t sk::launch_exact<0, N, 4>(const sk::ExactLaunch&);      \
   template cudaError_t sk::launch_exact<1, N, 3>(const sk::ExactLaunch&);      \
-  template cudaError_t sk::launch_exact<1, N, 4>(const sk::ExactLaunch&);      \
   template cudaError_t sk::launch_limb<0, N>(const sk::ExactLaunch&);          \
   template cudaError_t sk::launch_limb<1, N>(const sk::ExactLaunch&);

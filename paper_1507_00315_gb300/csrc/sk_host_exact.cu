@@ -19,9 +19,7 @@ namespace sk {
 
 #define SK_EXTERN_EXACT(N)                                                         \
   extern template cudaError_t launch_exact<0, N, 3>(const ExactLaunch&);          \
-  extern template cudaError_t launch_exact<0, N, 4>(const ExactLaunch&);          \
-  extern template cudaError_t launch_exact<1, N, 3>(const ExactLaunch&);          \
-  extern template cudaError_t launch_exact<1, N, 4>(const ExactLaunch&);
+  extern template cudaError_t launch_exact<1, N, 3>(const ExactLaunch&);
 SK_EXTERN_EXACT(1) SK_EXTERN_EXACT(2) SK_EXTERN_EXACT(3) SK_EXTERN_EXACT(4) SK_EXTERN_EXACT(5)
 SK_EXTERN_EXACT(6) SK_EXTERN_EXACT(7) SK_EXTERN_EXACT(8) SK_EXTERN_EXACT(9) SK_EXTERN_EXACT(10)
 SK_EXTERN_EXACT(11) SK_EXTERN_EXACT(12) SK_EXTERN_EXACT(13) SK_EXTERN_EXACT(14)
@@ -43,9 +41,9 @@ SK_EXTERN_LIMB(23) SK_EXTERN_LIMB(24) SK_EXTERN_LIMB(25) SK_EXTERN_LIMB(26)
 SK_EXTERN_LIMB(27) SK_EXTERN_LIMB(28)
 #undef SK_EXTERN_LIMB
 
-#define SK_ROW(N) {{launch_exact<0, N, 3>, launch_exact<0, N, 4>}, {launch_exact<1, N, 3>, launch_exact<1, N, 4>}}
-static const ExactLaunchFn kTable[kMaxN + 1][2][2] = {
-    {{nullptr, nullptr}, {nullptr, nullptr}},
+#define SK_ROW(N) {launch_exact<0, N, 3>, launch_exact<1, N, 3>}
+static const ExactLaunchFn kTable[kMaxN + 1][2] = {
+    {nullptr, nullptr},
     SK_ROW(1), SK_ROW(2), SK_ROW(3), SK_ROW(4), SK_ROW(5), SK_ROW(6), SK_ROW(7),
     SK_ROW(8), SK_ROW(9), SK_ROW(10), SK_ROW(11), SK_ROW(12), SK_ROW(13), SK_ROW(14),
     SK_ROW(15), SK_ROW(16), SK_ROW(17), SK_ROW(18), SK_ROW(19), SK_ROW(20), SK_ROW(21),
@@ -53,8 +51,8 @@ static const ExactLaunchFn kTable[kMaxN + 1][2][2] = {
 #undef SK_ROW
 
 ExactLaunchFn exact_launcher(int delta, int n, int nprimes) {
-  if (delta < 0 || delta > 1 || n < 1 || n > kMaxN || nprimes < 3 || nprimes > 4) return nullptr;
-  return kTable[n][delta][nprimes - 3];
+  if (delta < 0 || delta > 1 || n < 1 || n > kMaxN || nprimes != 3) return nullptr;
+  return kTable[n][delta];
 }
 
 #define SK_LROW(N) {launch_limb<0, N>, launch_limb<1, N>}
@@ -286,6 +284,37 @@ static void u128_half(sk_u128* v) {
   v->hi >>= 1;
 }
 
+int limb_max_m(int delta, int n) {
+  if (delta < 0 || delta > 1 || n < 1 || n > kMaxN) return 0;
+  return kLimbMaxM[n][delta];
+}
+
+// Output convention of a coefficient C (pairings, reflections distinct).
+// Sec. 1.3: no sequence of order n > 1 is its own reflection; the single
+// Skolem sequence of order 1 (1,1) is.
+int apply_convention(int variant, int n, int convention, sk_u128 coeff, sk_u128* out) {
+  sk_u128 v = coeff;
+  if (convention == SK_COUNT_REFLECTIONS_IDENTIFIED && variant != SK_HOOKED) {
+    if (variant == SK_SKOLEM && n == 1) {
+      v.lo += 1;
+    } else if (v.lo & 1) {
+      return SK_EMISMATCH;
+    }
+    u128_half(&v);
+  }
+  *out = v;
+  return SK_OK;
+}
+
+// CRT, checks and output convention of one job from its residues H mod p_i.
+int finalize_count(int variant, int n, int convention, int nprimes, const uint64_t* primes,
+                   const uint64_t* H, sk_u128* out) {
+  sk_u128 coeff = {0, 0};
+  int st = crt_coefficient(n, nprimes, primes, H, &coeff);
+  if (st) return st;
+  return apply_convention(variant, n, convention, coeff, out);
+}
+
 int count_impl(int variant, int n, const sk_count_opts* o, sk_u128* out, sk_count_report* rep) {
   auto t0 = std::chrono::steady_clock::now();
   Plan pl;
@@ -398,18 +427,9 @@ int count_impl(int variant, int n, const sk_count_opts* o, sk_u128* out, sk_coun
     rep->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   if (!complete) return SK_OK;
-  sk_u128 v = coeff;
-  const int conv = o ? o->convention : SK_COUNT_REFLECTIONS_IDENTIFIED;
-  if (conv == SK_COUNT_REFLECTIONS_IDENTIFIED && variant != SK_HOOKED) {
-    // Sec. 1.3: no sequence of order n > 1 is its own reflection; the single
-    // Skolem sequence of order 1 (1,1) is.
-    if (variant == SK_SKOLEM && n == 1) {
-      v.lo += 1;
-    } else if (v.lo & 1) {
-      return SK_EMISMATCH;
-    }
-    u128_half(&v);
-  }
+  sk_u128 v;
+  st = apply_convention(variant, n, o ? o->convention : SK_COUNT_REFLECTIONS_IDENTIFIED, coeff, &v);
+  if (st) return st;
   if (out) *out = v;
   return SK_OK;
 }

@@ -5,7 +5,8 @@
 // cudaMalloc can fail or fragment it under memory pressure), and
 // latency-sensitive host loops that cannot absorb the device-wide
 // synchronisation cudaFree implies.  This entry point runs the same
-// Gray-code kernel as skolem_item_residues, but its device scratch -- the
+// Gray-code kernel as skolem_item_residues (exact-limb form), but its device
+// scratch -- the
 // launch record (work counter, residue slots, error word) and the per-item
 // staging of the residues before they are copied to the caller's host
 // buffer -- lives in one file-scope __device__ array of fixed size, which
@@ -31,6 +32,7 @@
 namespace sk {
 
 unsigned long long position_mask(int variant, int n);   // sk_host_exact.cu
+int limb_max_m(int delta, int n);                       // sk_host_exact.cu
 
 namespace {
 
@@ -81,10 +83,10 @@ extern "C" int skolem_item_residues_noalloc(int variant, int n, int m, uint64_t 
   int st = prepare_primes(&o, &k, pv, &P);
   if (st) return st;
   const int F = 2 * n - 1, U = inner_bits(n), delta = variant == SK_LANGFORD ? 1 : 0;
-  if (m < U || m > F || F - m > 40) return SK_EINVAL;
+  if (m < U || m > F || m > limb_max_m(delta, n) || F - m > 40) return SK_EINVAL;
   const unsigned long long items = 1ULL << (F - m);
   if (q_lo >= items || count > items - q_lo) return SK_EINVAL;
-  ExactLaunchFn fn = exact_launcher(delta, n, k);
+  ExactLaunchFn fn = limb_launcher(delta, n);
   if (!fn) return SK_EINVAL;
   st = check_device();
   if (st) return st;
@@ -120,13 +122,5 @@ extern "C" int skolem_item_residues_noalloc(int variant, int n, int m, uint64_t 
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_status(e);
   if (h.err) return SK_ETIMEOUT;
-  // remove the Montgomery factor R^{-(g-2)} every term carries
-  GroupInfo gi = make_groups(delta, n);
-  const uint64_t ex = gi.g > 2 ? (uint64_t)(gi.g - 2) : 0;
-  for (int i = 0; i < k; ++i) {
-    const uint64_t R = (uint64_t)(((u128)1 << 32) % pv[i]);
-    const uint64_t f = powmod(R, ex, pv[i]);
-    for (uint64_t q = 0; q < count; ++q) out[q * k + i] = mulmod(out[q * k + i] % pv[i], f, pv[i]);
-  }
   return SK_OK;
 }

@@ -33,7 +33,7 @@ def test_small_orders_bit_exact_vs_backtracking(variant, arith):
 def test_residues_equal_oracle_sum(variant, arith):
     # H mod p of the whole half sum equals Algorithm 1's exact sum mod p.
     for n in (5, 9, 11):
-        _, rep = sk.count_ex(variant, n, nprimes=4, arith=arith)
+        _, rep = sk.count_ex(variant, n, nprimes=4 if arith == sk.ARITH_LIMBS else 3, arith=arith)
         H = oracle.signed_sum(variant, n, half=True, threads=8)
         for p, r in zip(rep["primes"], rep["residues"]):
             assert r == H % p
@@ -113,18 +113,18 @@ def test_large_orders_items_both_forms(variant, n, m):
     F = 2 * n - 1
     for q in (0, (1 << (F - m)) - 1, 0x5A5A5A5A5A5 % (1 << (F - m))):
         a = sk.item_residues(variant, n, m, q, 1, primes, arith=sk.ARITH_LIMBS)[0]
-        b = sk.item_residues(variant, n, m, q, 1, primes, arith=sk.ARITH_MONTGOMERY)[0]
+        b = sk.item_residues(variant, n, m, q, 1, primes[:3], arith=sk.ARITH_MONTGOMERY)[0]
         want = [oracle.partial_sum_mod(variant, n, m, q, p) for p in primes]
-        assert a == want and b == want, (q, a, b, want)
+        assert a == want and b == want[:3], (q, a, b, want)
 
 
 def test_schedule_independence():
     # walk width, block size and grid change the schedule, not the residues
-    base = sk.count_ex(SK, 13, nprimes=4)[1]["residues"]
+    base = sk.count_ex(SK, 13, nprimes=3)[1]["residues"]
     for kw in ({"walk_bits": 6}, {"walk_bits": 25}, {"block_threads": 64}, {"grid": 3},
                {"walk_bits": 9, "block_threads": 96, "grid": 7}, {"arith": sk.ARITH_MONTGOMERY},
                {"arith": sk.ARITH_MONTGOMERY, "walk_bits": 20, "block_threads": 128}):
-        assert sk.count_ex(SK, 13, nprimes=4, **kw)[1]["residues"] == base, kw
+        assert sk.count_ex(SK, 13, nprimes=3, **kw)[1]["residues"] == base, kw
 
 
 def test_custom_primes_and_check_prime():
@@ -146,6 +146,8 @@ def test_invalid_arguments():
         sk.count_ex(SK, 8, primes=[(1 << 61) - 1, 0, 0])
     with pytest.raises(sk.SkolemError):
         sk.count_ex(SK, 8, block_threads=100)
+    with pytest.raises(sk.SkolemError):          # Montgomery form: three moduli
+        sk.count_ex(SK, 8, nprimes=4, arith=sk.ARITH_MONTGOMERY)
 
 
 def test_checkpoint_resume(tmp_path):
