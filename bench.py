@@ -48,15 +48,40 @@ def groups(delta, n):
     return g
 
 
+def group_bits(delta, n):
+    """Bit lengths of the products of the bounds L_k = 2n - k - delta over the
+    groups 0..j (the kernel sizes its limbs from these)."""
+    bits, prod, g_prev, k0 = [], 1, None, 1
+    g, gp = 0, 1
+    starts = []
+    for k in range(1, n + 1):
+        L = max(2 * n - k - delta, 1)
+        if k == 1 or gp * L > 2147483647:
+            starts.append(k)
+            gp = 1
+        gp *= L
+    starts.append(n + 1)
+    for j in range(len(starts) - 1):
+        for k in range(starts[j], starts[j + 1]):
+            prod *= max(2 * n - k - delta, 1)
+        bits.append(prod.bit_length())
+    return bits
+
+
 def alg_ops_per_term(variant, n, nprimes=3):
-    """INT32 operations the method needs per term in this number system:
-    n correlation adds; n - g int32 multiplies inside the groups; the block
-    sign fold and the int64 head (2); per modulus, (g - 2) signed Montgomery
-    steps of 6 operations (two 32x32->64 products of the operand, m = lo * p',
-    two 32x32->64 products of m, one shift-add) and a 3-limb accumulate."""
+    """INT32 operations the exact-limb form needs per term: n correlation
+    adds; n - g int32 multiplies inside the groups; g absolute values; one
+    32x32 multiply per limb of each partial product after the first group;
+    the sign-masked add of the product (PL limbs) into the accumulator (AL
+    limbs).  The moduli enter once per work item, not per term."""
     delta = 1 if variant == 1 else 0
-    g = groups(delta, n)
-    return n + (n - g) + 2 + nprimes * (max(g - 2, 0) * 6 + 3)
+    bits = group_bits(delta, n)
+    g = len(bits)
+    limbs = [max(1, (b + 31) // 32) for b in bits]
+    muls = sum(limbs[1:])
+    PL = limbs[-1]
+    AL = (bits[-1] + 1 + 26 + 31) // 32
+    return n + (n - g) + g + muls + PL + AL
 
 
 # ------------------------------------------------------------------ clocks
@@ -181,6 +206,107 @@ def recorded_traffic():
     return None
 
 
+def recorded_imad_busy():
+    p = os.path.join(ROOT, "profiles", "exact_kernel_traffic.json")
+    try:
+        d = json.load(open(p))
+        if d.get("source_hash") == source_hash():
+            return d.get("fmaheavy_busy_frac")
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+def run_extra(args, world, rank, local):
+    """Extra workloads, one JSON line each: --config batch (all three
+    problems, n = 4..nmax, one persistent graph-captured launch vs one launch
+    per job) and --config large (S(24), L(24), four moduli, checkpointed)."""
+    import torch
+    import paper_1507_00315_gb300 as sk
+    torch.cuda.set_device(local)
+    sh = torch.cuda.current_stream().cuda_stream
+    if args.config == "batch":
+        jobs = [(v, n) for v in (0, 1, 2) for n in range(4, args.nmax + 1)]
+        out = {}
+        counts = None
+        for name, kw in (("per_job", {"mode": sk.BATCH_PER_JOB}), ("persistent_graph", {}),
+                         ("persistent_graph_autotuned", {"autotune": True})):
+            c, st, rep = sk.count_batch(jobs, repeats=max(1, args.steps), stream=sh, **kw)
+            assert counts is None or c == counts
+            counts = c
+            out[name] = {"kernel_ms_min": rep["kernel_ms_min"], "launches": rep["launches"],
+                         "terms_per_s": rep["terms"] / (rep["kernel_ms_min"] / 1e3),
+                         "block_threads": rep["block_threads"], "grid": rep["grid"],
+                         "wall_ms": rep["wall_ms"]}
+        line = {"metric": "batched sweep terms/s, persistent graph launch vs one launch per job",
+                "config": {"workload": f"{{Skolem, Langford, hooked}} x n=4..{args.nmax}, 3 moduli",
+                           "jobs": len(jobs)},
+                "unit": "terms/s", "results": out,
+                "speedup_persistent_vs_per_job": out["per_job"]["kernel_ms_min"] /
+                out["persistent_graph"]["kernel_ms_min"]}
+    elif args.config == "pt":
+        line = run_pt_bench(args, sk, sh)
+    else:
+        import tempfile
+        res = {}
+        for v, n in ((0, 24), (1, 24)):
+            path = os.path.join(args.ckpt_dir or tempfile.gettempdir(), f"sk_ckpt_{v}_{n}.txt")
+            c, rep = sk.count_ex(v, n, nprimes=4, checkpoint=path, stream=sh)
+            res[f"{'SL'[v]}({n})"] = {"count": str(c), "kernel_s": rep["kernel_ms"] / 1e3,
+                                      "wall_s": rep["wall_ms"] / 1e3, "chunks": rep["chunks_total"],
+                                      "resumed": rep["chunks_resumed"],
+                                      "terms_per_s": rep["terms"] / max(rep["kernel_ms"], 1e-9) * 1e3}
+        line = {"metric": "exact S(24), L(24): terms/s, checkpointed, 4 moduli",
+                "config": {"workload": "S(24), L(24), 2^47 terms each, 3 moduli + check modulus"},
+                "unit": "terms/s", "results": res}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+EXACT_S = {16: 700078384, 20: 5717789399488, 24: 102388058845620672}
+EXACT_L = {16: 326721800, 20: 2636337861200, 24: 46845158056515936}
+
+
+def run_pt_bench(args, sk, sh):
+    """Tempering: relative error against the exact counts (Tables 7 / 8)
+    versus GPU time, plain proposal and learned proposal (network trained on
+    plain-tempering samples), 32 temperatures x 4096 ladders."""
+    import numpy as np
+    cases = [(0, 16), (1, 16), (0, 20), (1, 20), (0, 24), (1, 24)][:args.pt_cases]
+    out = {}
+    for v, n in cases:
+        exact = (EXACT_S if v == 0 else EXACT_L)[n]
+        rows = []
+        for budget in args.pt_budgets:
+            est, rep = sk.pt_estimate(v, n, budget, ladders=4096, seed=budget, stream=sh)
+            rows.append({"proposal": "plain", "iterations": budget, "estimate": est,
+                         "rel_error": est / exact - 1, "gpu_ms": rep["kernel_ms"],
+                         "tune_ms": rep["tune_ms"]})
+        # training set: final states of independent plain runs on the tuned ladder
+        beta = sk.tune_ladder(v, n, 32, 32.0, 0)
+        states, seed = [], 100
+        while sum(len(x) for x in states) < args.pt_samples:
+            r = sk.pt_run(v, n, beta, 4096, 1000, 0, seed, want_final=True)
+            states.append(r["final_slots"].reshape(-1, n))
+            seed += 1
+        states = np.concatenate(states)[:args.pt_samples]
+        model = sk.Mlp(v, n, 131072, seed=1)
+        loss, train_ms = model.train(states, epochs=1, batch=4096, lr=1e-3, beta_star=2.0, seed=1)
+        for budget in args.pt_learned_budgets:
+            est, rep = sk.pt_estimate(v, n, budget, ladders=4096, seed=budget, beta=beta,
+                                      model=model, stream=sh)
+            rows.append({"proposal": "learned", "iterations": budget, "estimate": est,
+                         "rel_error": est / exact - 1, "gpu_ms": rep["kernel_ms"],
+                         "train_ms": train_ms, "train_loss": loss,
+                         "train_samples": int(states.shape[0])})
+        model.close()
+        out[f"{'SL'[v]}({n})"] = rows
+    return {"metric": "PT relative error vs GPU time, learned vs plain proposal",
+            "config": {"workload": "32 temperatures x 4096 ladders, Skolem / Langford n=16..24",
+                       "training": f"{args.pt_samples} plain-PT states, 1 epoch, Adam 1e-3"},
+            "unit": "relative error", "results": out}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -276,9 +402,10 @@ def run_ours(args, world, rank, local):
                    "block_threads": 256, "parallelism": f"{world} replica(s), one GPU each"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                      "frac": achieved / peak, "traffic": recorded_traffic(),
-                     "kernel": "exact_kernel<0,20,3> (S(20), 2^39 terms)",
+                     "kernel": "limb_kernel<0,20> (S(20), 2^39 terms)",
                      "ops_per_term": alg_ops_per_term(0, 20),
                      "peak_source": "measured: sk_int32_peak mode 1 (multiply-add / lop3 mix), same run",
+                     "imad_pipe_busy_ncu": recorded_imad_busy(),
                      "int32_mad_peak_tops": peak_mad / 1e12,
                      "all_launches_frac": (all_ops / (all_ms / 1e3) / 1e12) / peak},
         "e2e": {"value": e2e, "unit": "terms/s", "h2d_bytes_per_step": 0,
@@ -300,6 +427,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pt-budgets", type=int, nargs="+", default=[2000, 8000, 32000])
+    ap.add_argument("--pt-learned-budgets", type=int, nargs="+", default=[200, 800])
+    ap.add_argument("--pt-samples", type=int, default=10_000_000)
+    ap.add_argument("--pt-cases", type=int, default=6)
+    ap.add_argument("--config", default="mid", choices=["mid", "batch", "large", "pt"],
+                    help="mid: the headline workload; batch / large: extra measurements")
+    ap.add_argument("--nmax", type=int, default=22, help="largest n of --config batch")
+    ap.add_argument("--ckpt-dir", default=None, help="checkpoint directory of --config large")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -308,8 +443,8 @@ def main():
         run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
         return
     world, rank, local = dist_setup(args.gpus)
-    if False:
-        pass
+    if args.config != "mid":
+        run_extra(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -187,6 +187,107 @@ typedef struct sk_tune_result {
  * nprimes/primes/stream are read). */
 int skolem_autotune(int variant, int n, const sk_batch_opts *opts, sk_tune_result *out);
 
+/* ------------------------------------------------------ approximate count */
+
+/* Move proposals of the tempering chains.  SK_PT_PLAIN: Sec. 3 -- pair k
+ * uniform, its new start slot uniform among its other slots.  SK_PT_LEARNED:
+ * the move (k, slot) drawn from the softmax of a trained network over the
+ * bin occupancies, with the Metropolis-Hastings correction (not in the
+ * paper). */
+enum { SK_PT_PLAIN = 0, SK_PT_LEARNED = 1 };
+
+#define SK_PT_MAX_RUNGS 32
+
+typedef struct sk_pt_opts {
+  int rungs;              /* M temperatures, 1..32; 0 -> 32 */
+  int ladders;            /* independent ladders run side by side; 0 -> 4096 */
+  uint64_t seed;          /* Philox key */
+  double burnin_frac;     /* leading fraction of iterations not counted;
+                             0 -> 0.1, negative -> none */
+  const double *beta;     /* host, `rungs` non-decreasing inverse temperatures
+                             starting at 0; NULL -> pilot-tuned ladder */
+  double beta_max;        /* top of the tuned ladder; 0 -> 32 */
+  int proposal;           /* SK_PT_PLAIN (default) or SK_PT_LEARNED */
+  const void *model;      /* SK_PT_LEARNED: a model from sk_mlp_create */
+  void *stream;           /* cudaStream_t or NULL */
+} sk_pt_opts;
+
+typedef struct sk_pt_report {
+  int rungs, ladders;
+  uint64_t iterations, burnin;
+  double beta[SK_PT_MAX_RUNGS];      /* ladder used */
+  double ratio[SK_PT_MAX_RUNGS];     /* E[z_{j+1}/z_j] per rung (Table 6's
+                                        last column) */
+  double acc_move[SK_PT_MAX_RUNGS];  /* accepted moves per rung (W1) */
+  double acc_swap[SK_PT_MAX_RUNGS];  /* accepted exchanges of (j, j+1) (W2) */
+  double estimate;
+  double kernel_ms, tune_ms, wall_ms;
+} sk_pt_report;
+
+/* Approximate count by parallel tempering (Sec. 3, Algorithm 2): budget =
+ * iterations per ladder (each one move per rung plus one exchange phase),
+ * 1 <= budget < 2^32.  out (host): 1/2 Z(0) prod_j Ratio(j), reflections
+ * identified, with Z(0) = prod_k (2n - d_k).  Skolem and Langford,
+ * 2 <= n <= 40.  Deterministic for a given seed. */
+int pt_estimate(int variant, int n, uint64_t budget, double *out);
+int pt_estimate_ex(int variant, int n, uint64_t budget, const sk_pt_opts *opts, double *out,
+                   sk_pt_report *rep);
+
+/* The raw tempering run behind pt_estimate, for checks against a reference:
+ * L ladders of M rungs with the given ladder beta (host, M values) for
+ * `iters` iterations, statistics after `burnin`.  Host outputs: hist
+ * (M x (2n+1), counts of the energy E at each rung), acc_move / acc_swap
+ * (M, may be NULL), final_slots (L x M x n start bins of pair k = 1..n at
+ * each rung at the end, may be NULL). */
+int sk_pt_run(int variant, int n, int M, const double *beta, int L, uint64_t iters,
+              uint64_t burnin, uint64_t seed, uint64_t *hist, uint64_t *acc_move,
+              uint64_t *acc_swap, uint8_t *final_slots);
+
+/* The pilot-tuned ladder pt_estimate uses when opts->beta is NULL. */
+int sk_pt_tune_ladder(int variant, int n, int rungs, double beta_max, uint64_t seed,
+                      double *beta);
+
+/* ---------------------------------------------- learned move proposal */
+
+/* The move-proposal network of SK_PT_LEARNED (not in the paper): the 2n bin
+ * occupancies -> 256 ReLU -> 256 ReLU -> one logit per move (k, s), moves
+ * ordered by pair k then start slot s = 0..2n-d_k-1.  BF16 weights with FP32
+ * accumulation on the tensor cores, FP32 master weights, trained with Adam on
+ * the cross entropy against t(m) ~ exp(-beta* dE(m)) over the valid moves of
+ * each state (every move except a pair's current slot).
+ * Parameter layout on the host (float, row-major): W1 [2n][256], b1 [256],
+ * W2 [256][256], b2 [256], W3 [256][n_moves], b3 [n_moves]. */
+
+/* Creates a model for (variant, n) (Skolem or Langford, 2 <= n <= 40) with
+ * workspace for max_batch states (a multiple of 128), He-normal weights from
+ * `seed`.  *model receives an opaque handle owned by the caller; release it
+ * with sk_mlp_destroy. */
+int sk_mlp_create(int variant, int n, int max_batch, uint64_t seed, void **model);
+void sk_mlp_destroy(void *model);
+/* Number of moves (logits) and of host parameters. */
+int sk_mlp_dims(const void *model, int *n_moves, int *n_params);
+int sk_mlp_set_params(void *model, const float *params);   /* host, n_params */
+int sk_mlp_get_params(const void *model, float *params);   /* host, n_params */
+/* Logits of B <= max_batch states.  slots (host, B x n): start slot of pair
+ * k = 1..n of each state; logits (host, B x n_moves). */
+int sk_mlp_forward(void *model, const uint8_t *slots, int B, float *logits);
+/* Mean loss of a batch (B a multiple of 128) and its gradient (host,
+ * n_params, same layout as the parameters); the model is not updated. */
+int sk_mlp_loss_grad(void *model, const uint8_t *slots, int B, float beta_star, float *loss,
+                     float *grads);
+/* Adam training (lr, betas 0.9 / 0.999) on `count` states (host, count x n),
+ * `epochs` passes in minibatches of `batch` (multiple of 128) in an order
+ * shuffled by `seed`.  final_loss: mean loss of the last epoch; ms: device
+ * time (both may be NULL). */
+int sk_mlp_train(void *model, const uint8_t *states, uint64_t count, int epochs, int batch,
+                 float lr, float beta_star, uint64_t seed, float *final_loss, double *ms);
+/* The learned tempering run behind pt_estimate_ex with SK_PT_LEARNED, with
+ * the outputs of sk_pt_run (no final states).  Needs a model of the same
+ * (variant, n) whose max_batch >= L * M rounded up to 128. */
+int sk_pt_run_learned(int variant, int n, int M, const double *beta, int L, uint64_t iters,
+                      uint64_t burnin, uint64_t seed, const void *model, uint64_t *hist,
+                      uint64_t *acc_move, uint64_t *acc_swap);
+
 /* Residues of single work items, for sampled checks at full size.  Item q of
  * walk width m fixes the free variables m..2n-2 (bit b of q set means
  * x_{m+b+1} = -1) and runs the low m through all values; its sum is

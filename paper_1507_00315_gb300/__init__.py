@@ -120,6 +120,33 @@ class TuneResult(ctypes.Structure):
 
 
 BATCH_PERSISTENT, BATCH_PER_JOB = 0, 1
+PT_PLAIN, PT_LEARNED = 0, 1
+PT_MAX_RUNGS = 32
+
+
+class PtOpts(ctypes.Structure):
+    _fields_ = [("rungs", ctypes.c_int), ("ladders", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("burnin_frac", ctypes.c_double), ("beta", ctypes.POINTER(ctypes.c_double)),
+                ("beta_max", ctypes.c_double), ("proposal", ctypes.c_int),
+                ("model", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
+
+
+class PtReport(ctypes.Structure):
+    _fields_ = [("rungs", ctypes.c_int), ("ladders", ctypes.c_int),
+                ("iterations", ctypes.c_uint64), ("burnin", ctypes.c_uint64),
+                ("beta", ctypes.c_double * PT_MAX_RUNGS), ("ratio", ctypes.c_double * PT_MAX_RUNGS),
+                ("acc_move", ctypes.c_double * PT_MAX_RUNGS),
+                ("acc_swap", ctypes.c_double * PT_MAX_RUNGS),
+                ("estimate", ctypes.c_double), ("kernel_ms", ctypes.c_double),
+                ("tune_ms", ctypes.c_double), ("wall_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        M = self.rungs
+        return {"rungs": M, "ladders": self.ladders, "iterations": self.iterations,
+                "burnin": self.burnin, "beta": list(self.beta[:M]), "ratio": list(self.ratio[:M]),
+                "acc_move": list(self.acc_move[:M]), "acc_swap": list(self.acc_swap[:M]),
+                "estimate": self.estimate, "kernel_ms": self.kernel_ms,
+                "tune_ms": self.tune_ms, "wall_ms": self.wall_ms}
 
 _lib = None
 
@@ -150,6 +177,27 @@ def lib():
                                          ctypes.POINTER(BatchReport)]
         L.skolem_autotune.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(BatchOpts),
                                       ctypes.POINTER(TuneResult)]
+        vp, u64, dp = ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)
+        L.pt_estimate.argtypes = [ctypes.c_int, ctypes.c_int, u64, dp]
+        L.pt_estimate_ex.argtypes = [ctypes.c_int, ctypes.c_int, u64, ctypes.POINTER(PtOpts), dp,
+                                     ctypes.POINTER(PtReport)]
+        L.sk_pt_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, u64, u64,
+                                u64, vp, vp, vp, vp]
+        L.sk_pt_run_learned.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int,
+                                        u64, u64, u64, vp, vp, vp, vp]
+        L.sk_pt_tune_ladder.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        u64, vp]
+        L.sk_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, u64,
+                                    ctypes.POINTER(ctypes.c_void_p)]
+        L.sk_mlp_destroy.argtypes = [vp]
+        L.sk_mlp_destroy.restype = None
+        L.sk_mlp_dims.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.sk_mlp_set_params.argtypes = [vp, vp]
+        L.sk_mlp_get_params.argtypes = [vp, vp]
+        L.sk_mlp_forward.argtypes = [vp, vp, ctypes.c_int, vp]
+        L.sk_mlp_loss_grad.argtypes = [vp, vp, ctypes.c_int, ctypes.c_float, vp, vp]
+        L.sk_mlp_train.argtypes = [vp, vp, u64, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                   ctypes.c_float, u64, vp, vp]
         L.sk_int32_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double)]
         L.sk_default_primes.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
@@ -298,3 +346,141 @@ def autotune(variant, n: int, **kw):
     if st != SK_OK:
         raise SkolemError(st, "skolem_autotune")
     return {k: getattr(r, k) for k, _ in r._fields_}
+
+
+# ------------------------------------------------------------- tempering
+
+def _np():
+    import numpy as np
+    return np
+
+
+def pt_run(variant, n: int, beta, ladders: int, iters: int, burnin: int, seed: int,
+           want_final: bool = False, model=None):
+    """sk_pt_run (or sk_pt_run_learned with a model): dict(hist[M, 2n+1],
+    acc_move[M], acc_swap[M], final_slots[L, M, n] or None)."""
+    np = _np()
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    M = beta.shape[0]
+    hist = np.zeros((M, 2 * n + 1), dtype=np.uint64)
+    am = np.zeros(M, dtype=np.uint64)
+    asw = np.zeros(M, dtype=np.uint64)
+    if model is not None:
+        st = lib().sk_pt_run_learned(_variant(variant), n, M, beta.ctypes.data, ladders, iters,
+                                     burnin, seed, model.handle, hist.ctypes.data, am.ctypes.data,
+                                     asw.ctypes.data)
+        fin = None
+    else:
+        fin = np.zeros((ladders, M, n), dtype=np.uint8) if want_final else None
+        st = lib().sk_pt_run(_variant(variant), n, M, beta.ctypes.data, ladders, iters, burnin, seed,
+                             hist.ctypes.data, am.ctypes.data, asw.ctypes.data,
+                             fin.ctypes.data if fin is not None else None)
+    if st != SK_OK:
+        raise SkolemError(st, "sk_pt_run")
+    return {"hist": hist, "acc_move": am, "acc_swap": asw, "final_slots": fin}
+
+
+def tune_ladder(variant, n: int, rungs: int = 32, beta_max: float = 32.0, seed: int = 0):
+    np = _np()
+    b = np.zeros(rungs, dtype=np.float64)
+    st = lib().sk_pt_tune_ladder(_variant(variant), n, rungs, beta_max, seed, b.ctypes.data)
+    if st != SK_OK:
+        raise SkolemError(st, "sk_pt_tune_ladder")
+    return b
+
+
+def pt_estimate(variant, n: int, budget: int, rungs=0, ladders=0, seed=0, burnin_frac=0.0,
+                beta=None, beta_max=0.0, model=None, stream=None):
+    """pt_estimate_ex: (estimate, report dict)."""
+    np = _np()
+    o = PtOpts()
+    o.rungs, o.ladders, o.seed, o.burnin_frac, o.beta_max = rungs, ladders, seed, burnin_frac, beta_max
+    keep = None
+    if beta is not None:
+        keep = np.ascontiguousarray(beta, dtype=np.float64)
+        o.rungs = keep.shape[0]
+        o.beta = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    if model is not None:
+        o.proposal = PT_LEARNED
+        o.model = model.handle
+    o.stream = stream
+    out = ctypes.c_double()
+    rep = PtReport()
+    st = lib().pt_estimate_ex(_variant(variant), n, budget, ctypes.byref(o), ctypes.byref(out),
+                              ctypes.byref(rep))
+    if st != SK_OK:
+        raise SkolemError(st, "pt_estimate_ex")
+    return out.value, rep.as_dict()
+
+
+class Mlp:
+    """Handle of the move-proposal network (sk_mlp_*)."""
+
+    def __init__(self, variant, n: int, max_batch: int = 4096, seed: int = 0):
+        h = ctypes.c_void_p()
+        st = lib().sk_mlp_create(_variant(variant), n, max_batch, seed, ctypes.byref(h))
+        if st != SK_OK:
+            raise SkolemError(st, "sk_mlp_create")
+        self.handle, self.n, self.variant = h.value, n, _variant(variant)
+        nm, npar = ctypes.c_int(), ctypes.c_int()
+        lib().sk_mlp_dims(self.handle, ctypes.byref(nm), ctypes.byref(npar))
+        self.n_moves, self.n_params = nm.value, npar.value
+
+    def close(self):
+        if self.handle:
+            lib().sk_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat):
+        np = _np()
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.n_params
+        st = lib().sk_mlp_set_params(self.handle, a.ctypes.data)
+        if st != SK_OK:
+            raise SkolemError(st, "sk_mlp_set_params")
+
+    def get_params(self):
+        np = _np()
+        a = np.zeros(self.n_params, dtype=np.float32)
+        st = lib().sk_mlp_get_params(self.handle, a.ctypes.data)
+        if st != SK_OK:
+            raise SkolemError(st, "sk_mlp_get_params")
+        return a
+
+    def forward(self, slots):
+        np = _np()
+        s = np.ascontiguousarray(slots, dtype=np.uint8)
+        out = np.zeros((s.shape[0], self.n_moves), dtype=np.float32)
+        st = lib().sk_mlp_forward(self.handle, s.ctypes.data, s.shape[0], out.ctypes.data)
+        if st != SK_OK:
+            raise SkolemError(st, "sk_mlp_forward")
+        return out
+
+    def loss_grad(self, slots, beta_star: float):
+        np = _np()
+        s = np.ascontiguousarray(slots, dtype=np.uint8)
+        loss = np.zeros(1, dtype=np.float32)
+        g = np.zeros(self.n_params, dtype=np.float32)
+        st = lib().sk_mlp_loss_grad(self.handle, s.ctypes.data, s.shape[0], beta_star,
+                                    loss.ctypes.data, g.ctypes.data)
+        if st != SK_OK:
+            raise SkolemError(st, "sk_mlp_loss_grad")
+        return float(loss[0]), g
+
+    def train(self, states, epochs: int = 1, batch: int = 4096, lr: float = 1e-3,
+              beta_star: float = 2.0, seed: int = 0):
+        np = _np()
+        s = np.ascontiguousarray(states, dtype=np.uint8)
+        loss = np.zeros(1, dtype=np.float32)
+        ms = np.zeros(1, dtype=np.float64)
+        st = lib().sk_mlp_train(self.handle, s.ctypes.data, s.shape[0], epochs, batch, lr,
+                                beta_star, seed, loss.ctypes.data, ms.ctypes.data)
+        if st != SK_OK:
+            raise SkolemError(st, "sk_mlp_train")
+        return float(loss[0]), float(ms[0])

@@ -334,9 +334,12 @@ int count_impl(int variant, int n, const sk_count_opts* o, sk_u128* out, sk_coun
   unsigned long long chunk = (o && o->chunk_items) ? o->chunk_items : 0;
   if (!chunk) {
     if (ckpt_on) {
-      // about 2^37 terms per launch (~1 s on one GB300 at n = 24)
+      // about 2^37 terms per launch, but at least 2^22 items so that each of
+      // the ~80k resident threads gets dozens of items and the last wave of a
+      // launch stays short
       int lg = 37 - pl.m;
-      chunk = lg <= 0 ? 1ULL : (lg >= 40 ? pl.items : (1ULL << lg));
+      if (lg < 22) lg = 22;
+      chunk = lg >= 40 ? pl.items : (1ULL << lg);
     } else {
       chunk = pl.items;
     }

@@ -1,0 +1,539 @@
+// sk_mlp.cu -- the move-proposal network of the learned tempering chains
+// (an addition to Sec. 3): occupancy of the 2n bins -> 256 ReLU -> 256 ReLU
+// -> one logit per move (k, s), BF16 weights with FP32 accumulation and FP32
+// master weights, trained on the GPU with hand-written forward/backward and
+// Adam.  Target of a state C: t(m) ~ exp(-beta* dE(m)) over its valid moves;
+// loss: cross entropy of the masked softmax.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "sk_gemm.cuh"
+#include "sk_host_common.h"
+#include "sk_mlp.cuh"
+
+namespace sk {
+
+template <bool AT, bool BT, int EPI>
+cudaError_t gemm(const GemmArgs& g, int splits, cudaStream_t s) {
+  if (g.M % kGBM || g.N % kGBN || g.K % (kGBK * splits)) return cudaErrorInvalidValue;
+  dim3 grid(g.N / kGBN, g.M / kGBM, splits);
+  gemm_bf16_kernel<AT, BT, EPI><<<grid, 256, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+// X[b][i] = occupancy of bin i of state b (0 beyond 2n).
+__global__ void mlp_inputs_kernel(const unsigned char* __restrict__ slots, int B, int n, int delta,
+                                  int K1, __nv_bfloat16* X) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  unsigned char occ[2 * kPtMaxN];
+  for (int i = 0; i < 2 * n; ++i) occ[i] = 0;
+  for (int k = 1; k <= n; ++k) {
+    const int s = slots[(size_t)b * n + (k - 1)];
+    occ[s] += 1;
+    occ[s + k + delta] += 1;
+  }
+  __nv_bfloat16* x = X + (size_t)b * K1;
+  for (int i = 0; i < K1; ++i) x[i] = __float2bfloat16(i < 2 * n ? (float)occ[i] : 0.f);
+}
+
+// out[c] += sum over rows of in[r][c] (bias gradients).
+__global__ void colsum_kernel(const __nv_bfloat16* __restrict__ in, int rows, int cols,
+                              int rows_per_block, float* out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  const int r0 = blockIdx.y * rows_per_block;
+  const int r1 = min(rows, r0 + rows_per_block);
+  float acc = 0.f;
+  for (int r = r0; r < r1; ++r) acc += __bfloat162float(in[(size_t)r * cols + c]);
+  atomicAdd(&out[c], acc);
+}
+
+// Adam (Kingma & Ba 2015) over the flat parameter vector; refreshes the bf16
+// copies of the weight matrices.
+__global__ void adam_kernel(float* w, const float* g, float* m, float* v, size_t count, float lr,
+                            float b1, float b2, float eps, float c1, float c2,
+                            __nv_bfloat16* wb, size_t nweights_b) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    if (i < nweights_b) wb[i] = __float2bfloat16(wi);
+  }
+}
+
+__global__ void f32_to_bf16_kernel(const float* in, __nv_bfloat16* out, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = __float2bfloat16(in[i]);
+}
+
+}  // namespace sk
+
+namespace sk {
+
+// One warp per state: target t(m) ~ exp(-beta* dE(m)) over the valid moves,
+// q = masked softmax of the logits, dZ = (q - t) / B, loss += -sum t log q / B.
+__global__ void __launch_bounds__(256)
+    mlp_loss_kernel(const float* __restrict__ Z, int ldz, const unsigned char* __restrict__ slots,
+                    int B, MoveTable mt, float beta_star, float inv_B, __nv_bfloat16* dZ,
+                    float* loss) {
+  __shared__ unsigned char s_occ[8][2 * kPtMaxN];
+  __shared__ unsigned char s_slot[8][kPtMaxN + 1];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int b = blockIdx.x * 8 + w;
+  if (b >= B) return;
+  const int n = mt.n, bins = 2 * n;
+  for (int i = lane; i < bins; i += 32) s_occ[w][i] = 0;
+  __syncwarp();
+  if (lane == 0) {
+    for (int k = 1; k <= n; ++k) {
+      const int s = slots[(size_t)b * n + (k - 1)];
+      s_slot[w][k] = (unsigned char)s;
+      s_occ[w][s] += 1;
+      s_occ[w][s + k + mt.delta] += 1;
+    }
+  }
+  __syncwarp();
+  const float* z = Z + (size_t)b * ldz;
+  float zmax = -INFINITY, wmax = -INFINITY;
+  for (int m = lane, k = 1; m < mt.NM; m += 32) {
+    while (m >= mt.off[k + 1]) ++k;
+    const int s = m - mt.off[k], sk = s_slot[w][k];
+    if (s == sk) continue;
+    const int de = move_delta_e(s_occ[w], sk, k + mt.delta, s);
+    zmax = fmaxf(zmax, z[m]);
+    wmax = fmaxf(wmax, -beta_star * (float)de);
+  }
+  zmax = warp_max(zmax);
+  wmax = warp_max(wmax);
+  float sq = 0.f, stt = 0.f;
+  for (int m = lane, k = 1; m < mt.NM; m += 32) {
+    while (m >= mt.off[k + 1]) ++k;
+    const int s = m - mt.off[k], sk = s_slot[w][k];
+    if (s == sk) continue;
+    const int de = move_delta_e(s_occ[w], sk, k + mt.delta, s);
+    sq += __expf(z[m] - zmax);
+    stt += __expf(-beta_star * (float)de - wmax);
+  }
+  sq = warp_sum(sq);
+  stt = warp_sum(stt);
+  const float lse = zmax + __logf(sq);
+  float l = 0.f;
+  __nv_bfloat16* dz = dZ + (size_t)b * ldz;
+  for (int m = lane, k = 1; m < ldz; m += 32) {
+    if (m >= mt.NM) { dz[m] = __float2bfloat16(0.f); continue; }
+    while (m >= mt.off[k + 1]) ++k;
+    const int s = m - mt.off[k], sk = s_slot[w][k];
+    if (s == sk) { dz[m] = __float2bfloat16(0.f); continue; }
+    const int de = move_delta_e(s_occ[w], sk, k + mt.delta, s);
+    const float q = __expf(z[m] - lse);
+    const float t = __expf(-beta_star * (float)de - wmax) / stt;
+    dz[m] = __float2bfloat16((q - t) * inv_B);
+    l -= t * (z[m] - lse);
+  }
+  l = warp_sum(l);
+  if (lane == 0) atomicAdd(loss, l * inv_B);
+}
+
+MoveTable move_table(const Mlp& m) {
+  MoveTable t;
+  std::memset(&t, 0, sizeof(t));
+  t.n = m.n;
+  t.delta = m.delta;
+  t.NM = m.NM;
+  for (int k = 1; k <= m.n + 1; ++k) t.off[k] = m.off[k];
+  return t;
+}
+
+// Forward pass for B (multiple of 128) states whose slots are already in
+// m.slots: X, H1, H2 (bf16) and Z (fp32 logits).
+cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s) {
+  mlp_inputs_kernel<<<(B + 127) / 128, 128, 0, s>>>(m.slots, B, m.n, m.delta, m.K1, m.X);
+  GemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.M = B; g.N = kHidden; g.K = m.K1; g.A = m.X; g.lda = m.K1; g.B = m.W1; g.ldb = kHidden;
+  g.C = m.H1; g.ldc = kHidden; g.bias = m.b1;
+  cudaError_t e = gemm<false, false, EPI_BF16_RELU>(g, 1, s);
+  if (e != cudaSuccess) return e;
+  g.K = kHidden; g.A = m.H1; g.lda = kHidden; g.B = m.W2; g.C = m.H2; g.bias = m.b2;
+  e = gemm<false, false, EPI_BF16_RELU>(g, 1, s);
+  if (e != cudaSuccess) return e;
+  g.N = m.NMp; g.A = m.H2; g.B = m.W3; g.ldb = m.NMp; g.C = m.Z; g.ldc = m.NMp; g.bias = m.b3;
+  return gemm<false, false, EPI_F32>(g, 1, s);
+}
+
+int splits_for(int K) {
+  int sp = 1;
+  while (sp < 16 && K % (kGBK * sp * 2) == 0 && K / (sp * 2) >= 256) sp *= 2;
+  return sp;
+}
+
+// Loss and gradients of a batch (after mlp_forward_dev): gW*, gb* (fp32).
+cudaError_t mlp_backward_dev(Mlp& m, int B, float beta_star, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(m.gW1, 0, m.nparams * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m.loss, 0, sizeof(float), s);
+  if (e != cudaSuccess) return e;
+  mlp_loss_kernel<<<(B + 7) / 8, 256, 0, s>>>(m.Z, m.NMp, m.slots, B, move_table(m), beta_star,
+                                              1.0f / (float)B, m.dZ, m.loss);
+  GemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  const int sp = splits_for(B);
+  // dW3 = H2^T dZ
+  g.M = kHidden; g.N = m.NMp; g.K = B; g.A = m.H2; g.lda = kHidden; g.B = m.dZ; g.ldb = m.NMp;
+  g.C = m.gW3; g.ldc = m.NMp;
+  e = gemm<true, false, EPI_ATOMIC>(g, sp, s);
+  if (e != cudaSuccess) return e;
+  // dH2 = (dZ W3^T) * [H2 > 0]
+  std::memset(&g, 0, sizeof(g));
+  g.M = B; g.N = kHidden; g.K = m.NMp; g.A = m.dZ; g.lda = m.NMp; g.B = m.W3; g.ldb = m.NMp;
+  g.C = m.dH2; g.ldc = kHidden; g.aux = m.H2;
+  e = gemm<false, true, EPI_BF16_MASK>(g, 1, s);
+  if (e != cudaSuccess) return e;
+  // dW2 = H1^T dH2
+  std::memset(&g, 0, sizeof(g));
+  g.M = kHidden; g.N = kHidden; g.K = B; g.A = m.H1; g.lda = kHidden; g.B = m.dH2;
+  g.ldb = kHidden; g.C = m.gW2; g.ldc = kHidden;
+  e = gemm<true, false, EPI_ATOMIC>(g, sp, s);
+  if (e != cudaSuccess) return e;
+  // dH1 = (dH2 W2^T) * [H1 > 0]
+  std::memset(&g, 0, sizeof(g));
+  g.M = B; g.N = kHidden; g.K = kHidden; g.A = m.dH2; g.lda = kHidden; g.B = m.W2;
+  g.ldb = kHidden; g.C = m.dH1; g.ldc = kHidden; g.aux = m.H1;
+  e = gemm<false, true, EPI_BF16_MASK>(g, 1, s);
+  if (e != cudaSuccess) return e;
+  // dW1 = X^T dH1
+  std::memset(&g, 0, sizeof(g));
+  g.M = m.K1; g.N = kHidden; g.K = B; g.A = m.X; g.lda = m.K1; g.B = m.dH1; g.ldb = kHidden;
+  g.C = m.gW1; g.ldc = kHidden;
+  e = gemm<true, false, EPI_ATOMIC>(g, sp, s);
+  if (e != cudaSuccess) return e;
+  // bias gradients: column sums
+  const int rpb = 512;
+  colsum_kernel<<<dim3((m.NMp + 127) / 128, (B + rpb - 1) / rpb), 128, 0, s>>>(m.dZ, B, m.NMp, rpb, m.gb3);
+  colsum_kernel<<<dim3(kHidden / 128, (B + rpb - 1) / rpb), 128, 0, s>>>(m.dH2, B, kHidden, rpb, m.gb2);
+  colsum_kernel<<<dim3(kHidden / 128, (B + rpb - 1) / rpb), 128, 0, s>>>(m.dH1, B, kHidden, rpb, m.gb1);
+  return cudaGetLastError();
+}
+
+}  // namespace sk
+
+namespace sk {
+
+__global__ void gather_slots_kernel(const unsigned char* __restrict__ all, const unsigned* __restrict__ idx,
+                                    int B, int n, unsigned char* out) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= (size_t)B * n) return;
+  const size_t b = i / n, k = i % n;
+  out[i] = all[(size_t)idx[b] * n + k];
+}
+
+static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+int mlp_create(int variant, int n, int max_batch, uint64_t seed, Mlp** out) {
+  if (variant != SK_SKOLEM && variant != SK_LANGFORD) return SK_EINVAL;
+  if (n < 2 || n > kPtMaxN || max_batch < 128 || max_batch % 128) return SK_EINVAL;
+  int st = check_device();
+  if (st) return st;
+  Mlp* m = new Mlp;
+  std::memset(m, 0, sizeof(*m));
+  m->variant = variant;
+  m->n = n;
+  m->delta = variant == SK_LANGFORD ? 1 : 0;
+  m->bins = 2 * n;
+  m->K1 = 128;
+  m->max_batch = max_batch;
+  m->off[1] = 0;
+  for (int k = 1; k <= n; ++k) m->off[k + 1] = m->off[k] + (2 * n - (k + m->delta));
+  m->NM = m->off[n + 1];
+  m->NMp = (m->NM + 127) / 128 * 128;
+  const size_t w1 = (size_t)m->K1 * kHidden, w2 = (size_t)kHidden * kHidden,
+               w3 = (size_t)kHidden * m->NMp;
+  m->nparams = w1 + w2 + w3 + 2 * kHidden + m->NMp;
+  const size_t B = (size_t)max_batch;
+  size_t off = 0;
+  const size_t o_par = off; off = al256(off + m->nparams * 4);
+  const size_t o_grad = off; off = al256(off + m->nparams * 4);
+  const size_t o_am = off; off = al256(off + m->nparams * 4);
+  const size_t o_av = off; off = al256(off + m->nparams * 4);
+  const size_t o_wb = off; off = al256(off + (w1 + w2 + w3) * 2);
+  const size_t o_sl = off; off = al256(off + B * n);
+  const size_t o_x = off; off = al256(off + B * m->K1 * 2);
+  const size_t o_h1 = off; off = al256(off + B * kHidden * 2);
+  const size_t o_h2 = off; off = al256(off + B * kHidden * 2);
+  const size_t o_dh1 = off; off = al256(off + B * kHidden * 2);
+  const size_t o_dh2 = off; off = al256(off + B * kHidden * 2);
+  const size_t o_dz = off; off = al256(off + B * m->NMp * 2);
+  const size_t o_z = off; off = al256(off + B * m->NMp * 4);
+  const size_t o_loss = off; off = al256(off + 4);
+  char* p = nullptr;
+  if (cudaMalloc(&p, off) != cudaSuccess) {
+    delete m;
+    return SK_ENOMEM;
+  }
+  m->block = p;
+  float* par = (float*)(p + o_par);
+  m->mW1 = par; m->mW2 = par + w1; m->mW3 = par + w1 + w2;
+  m->b1 = par + w1 + w2 + w3; m->b2 = m->b1 + kHidden; m->b3 = m->b2 + kHidden;
+  float* gr = (float*)(p + o_grad);
+  m->gW1 = gr; m->gW2 = gr + w1; m->gW3 = gr + w1 + w2;
+  m->gb1 = gr + w1 + w2 + w3; m->gb2 = m->gb1 + kHidden; m->gb3 = m->gb2 + kHidden;
+  m->am = (float*)(p + o_am);
+  m->av = (float*)(p + o_av);
+  __nv_bfloat16* wb = (__nv_bfloat16*)(p + o_wb);
+  m->W1 = wb; m->W2 = wb + w1; m->W3 = wb + w1 + w2;
+  m->slots = (unsigned char*)(p + o_sl);
+  m->X = (__nv_bfloat16*)(p + o_x);
+  m->H1 = (__nv_bfloat16*)(p + o_h1);
+  m->H2 = (__nv_bfloat16*)(p + o_h2);
+  m->dH1 = (__nv_bfloat16*)(p + o_dh1);
+  m->dH2 = (__nv_bfloat16*)(p + o_dh2);
+  m->dZ = (__nv_bfloat16*)(p + o_dz);
+  m->Z = (float*)(p + o_z);
+  m->loss = (float*)(p + o_loss);
+  // He-normal initial weights (input rows beyond 2n and move columns beyond
+  // NM stay zero), zero biases
+  std::vector<float> h(m->nparams, 0.f);
+  std::mt19937_64 rng(seed);
+  std::normal_distribution<float> nd(0.f, 1.f);
+  const float s1 = std::sqrt(2.f / (float)m->bins), s2 = std::sqrt(2.f / kHidden),
+              s3 = std::sqrt(1.f / kHidden);
+  for (int i = 0; i < m->bins; ++i)
+    for (int j = 0; j < kHidden; ++j) h[(size_t)i * kHidden + j] = s1 * nd(rng);
+  for (size_t i = 0; i < w2; ++i) h[w1 + i] = s2 * nd(rng);
+  for (int i = 0; i < kHidden; ++i)
+    for (int j = 0; j < m->NM; ++j) h[w1 + w2 + (size_t)i * m->NMp + j] = s3 * nd(rng);
+  cudaError_t e = cudaMemcpy(par, h.data(), m->nparams * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(m->am, 0, m->nparams * 4);
+  if (e == cudaSuccess) e = cudaMemset(m->av, 0, m->nparams * 4);
+  if (e == cudaSuccess) {
+    f32_to_bf16_kernel<<<256, 256>>>(par, wb, w1 + w2 + w3);
+    e = cudaDeviceSynchronize();
+  }
+  if (e != cudaSuccess) {
+    cudaFree(p);
+    delete m;
+    return cuda_status(e);
+  }
+  *out = m;
+  return SK_OK;
+}
+
+// Host parameter layout (unpadded, as in the reference): W1 [2n][256], b1
+// [256], W2 [256][256], b2 [256], W3 [256][NM], b3 [NM].
+size_t host_param_count(const Mlp& m) {
+  return (size_t)m.bins * kHidden + kHidden + (size_t)kHidden * kHidden + kHidden +
+         (size_t)kHidden * m.NM + m.NM;
+}
+
+// dev (padded layout W1|W2|W3|b1|b2|b3) <-> host (unpadded W1|b1|W2|b2|W3|b3)
+void pack_host(const Mlp& m, const float* dev_flat, float* host) {
+  const size_t w1 = (size_t)m.K1 * kHidden, w2 = (size_t)kHidden * kHidden,
+               w3 = (size_t)kHidden * m.NMp;
+  size_t o = 0;
+  for (int i = 0; i < m.bins; ++i)
+    for (int j = 0; j < kHidden; ++j) host[o++] = dev_flat[(size_t)i * kHidden + j];
+  for (int j = 0; j < kHidden; ++j) host[o++] = dev_flat[w1 + w2 + w3 + j];
+  for (size_t i = 0; i < w2; ++i) host[o++] = dev_flat[w1 + i];
+  for (int j = 0; j < kHidden; ++j) host[o++] = dev_flat[w1 + w2 + w3 + kHidden + j];
+  for (int i = 0; i < kHidden; ++i)
+    for (int j = 0; j < m.NM; ++j) host[o++] = dev_flat[w1 + w2 + (size_t)i * m.NMp + j];
+  for (int j = 0; j < m.NM; ++j) host[o++] = dev_flat[w1 + w2 + w3 + 2 * kHidden + j];
+}
+
+void unpack_host(const Mlp& m, const float* host, float* dev_flat) {
+  const size_t w1 = (size_t)m.K1 * kHidden, w2 = (size_t)kHidden * kHidden,
+               w3 = (size_t)kHidden * m.NMp;
+  std::memset(dev_flat, 0, m.nparams * 4);
+  size_t o = 0;
+  for (int i = 0; i < m.bins; ++i)
+    for (int j = 0; j < kHidden; ++j) dev_flat[(size_t)i * kHidden + j] = host[o++];
+  for (int j = 0; j < kHidden; ++j) dev_flat[w1 + w2 + w3 + j] = host[o++];
+  for (size_t i = 0; i < w2; ++i) dev_flat[w1 + i] = host[o++];
+  for (int j = 0; j < kHidden; ++j) dev_flat[w1 + w2 + w3 + kHidden + j] = host[o++];
+  for (int i = 0; i < kHidden; ++i)
+    for (int j = 0; j < m.NM; ++j) dev_flat[w1 + w2 + (size_t)i * m.NMp + j] = host[o++];
+  for (int j = 0; j < m.NM; ++j) dev_flat[w1 + w2 + w3 + 2 * kHidden + j] = host[o++];
+}
+
+// Copies B host states into m.slots (zero states pad up to a multiple of
+// 128) and returns the padded count.
+int upload_states(Mlp& m, const uint8_t* slots, int B, cudaStream_t s, cudaError_t* e) {
+  const int Bp = (B + 127) / 128 * 128;
+  *e = cudaMemsetAsync(m.slots, 0, (size_t)Bp * m.n, s);
+  if (*e == cudaSuccess) *e = cudaMemcpyAsync(m.slots, slots, (size_t)B * m.n, cudaMemcpyHostToDevice, s);
+  return Bp;
+}
+
+}  // namespace sk
+
+using sk::Mlp;
+
+extern "C" int sk_mlp_create(int variant, int n, int max_batch, uint64_t seed, void** model) {
+  if (!model) return SK_EINVAL;
+  Mlp* m = nullptr;
+  int st = sk::mlp_create(variant, n, max_batch, seed, &m);
+  if (st == SK_OK) *model = m;
+  return st;
+}
+
+extern "C" void sk_mlp_destroy(void* model) {
+  Mlp* m = (Mlp*)model;
+  if (!m) return;
+  cudaFree(m->block);
+  delete m;
+}
+
+extern "C" int sk_mlp_dims(const void* model, int* n_moves, int* n_params) {
+  const Mlp* m = (const Mlp*)model;
+  if (!m) return SK_EINVAL;
+  if (n_moves) *n_moves = m->NM;
+  if (n_params) *n_params = (int)sk::host_param_count(*m);
+  return SK_OK;
+}
+
+extern "C" int sk_mlp_set_params(void* model, const float* params) {
+  Mlp* m = (Mlp*)model;
+  if (!m || !params) return SK_EINVAL;
+  std::vector<float> d(m->nparams);
+  sk::unpack_host(*m, params, d.data());
+  cudaError_t e = cudaMemcpy(m->mW1, d.data(), m->nparams * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(m->am, 0, m->nparams * 4);
+  if (e == cudaSuccess) e = cudaMemset(m->av, 0, m->nparams * 4);
+  if (e == cudaSuccess) {
+    sk::f32_to_bf16_kernel<<<256, 256>>>(m->mW1, m->W1, m->nparams - 2 * sk::kHidden - m->NMp);
+    e = cudaDeviceSynchronize();
+  }
+  m->adam_t = 0;
+  return sk::cuda_status(e);
+}
+
+extern "C" int sk_mlp_get_params(const void* model, float* params) {
+  const Mlp* m = (const Mlp*)model;
+  if (!m || !params) return SK_EINVAL;
+  std::vector<float> d(m->nparams);
+  cudaError_t e = cudaMemcpy(d.data(), m->mW1, m->nparams * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return sk::cuda_status(e);
+  sk::pack_host(*m, d.data(), params);
+  return SK_OK;
+}
+
+extern "C" int sk_mlp_forward(void* model, const uint8_t* slots, int B, float* logits) {
+  Mlp* m = (Mlp*)model;
+  if (!m || !slots || !logits || B < 1 || B > m->max_batch) return SK_EINVAL;
+  cudaError_t e;
+  const int Bp = sk::upload_states(*m, slots, B, nullptr, &e);
+  if (e == cudaSuccess) e = sk::mlp_forward_dev(*m, Bp, nullptr);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2D(logits, (size_t)m->NM * 4, m->Z, (size_t)m->NMp * 4, (size_t)m->NM * 4, B,
+                     cudaMemcpyDeviceToHost);
+  return sk::cuda_status(e);
+}
+
+extern "C" int sk_mlp_loss_grad(void* model, const uint8_t* slots, int B, float beta_star,
+                                float* loss, float* grads) {
+  Mlp* m = (Mlp*)model;
+  if (!m || !slots || B < 128 || B % 128 || B > m->max_batch) return SK_EINVAL;
+  cudaError_t e;
+  sk::upload_states(*m, slots, B, nullptr, &e);
+  if (e == cudaSuccess) e = sk::mlp_forward_dev(*m, B, nullptr);
+  if (e == cudaSuccess) e = sk::mlp_backward_dev(*m, B, beta_star, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return sk::cuda_status(e);
+  if (loss) cudaMemcpy(loss, m->loss, 4, cudaMemcpyDeviceToHost);
+  if (grads) {
+    std::vector<float> d(m->nparams);
+    e = cudaMemcpy(d.data(), m->gW1, m->nparams * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return sk::cuda_status(e);
+    sk::pack_host(*m, d.data(), grads);
+  }
+  return SK_OK;
+}
+
+namespace sk {
+
+int mlp_train_impl(Mlp& m, const uint8_t* states, uint64_t count, int epochs, int batch, float lr,
+                   float beta_star, uint64_t seed, float* final_loss, double* ms_out) {
+  if (!states || count < (uint64_t)batch || epochs < 1 || batch < 128 || batch % 128 ||
+      batch > m.max_batch || !(lr > 0))
+    return SK_EINVAL;
+  const uint64_t steps = count / (uint64_t)batch;
+  unsigned char* dstates = nullptr;
+  unsigned* didx = nullptr;
+  float* hloss = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&dstates, count * m.n);
+  if (e == cudaSuccess) e = cudaMalloc(&didx, count * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaHostAlloc(&hloss, steps * sizeof(float), cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaMemcpy(dstates, states, count * m.n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  std::vector<unsigned> perm(count);
+  for (uint64_t i = 0; i < count; ++i) perm[i] = (unsigned)i;
+  std::mt19937_64 rng(seed);
+  const size_t nwb = (size_t)m.K1 * kHidden + (size_t)kHidden * kHidden + (size_t)kHidden * m.NMp;
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  double last = 0.0;
+  for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+    std::shuffle(perm.begin(), perm.end(), rng);
+    e = cudaMemcpyAsync(didx, perm.data(), count * sizeof(unsigned), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // perm is reused next epoch
+    for (uint64_t st = 0; st < steps && e == cudaSuccess; ++st) {
+      const size_t tot = (size_t)batch * m.n;
+      gather_slots_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(dstates, didx + st * batch,
+                                                                       batch, m.n, m.slots);
+      e = mlp_forward_dev(m, batch, s);
+      if (e == cudaSuccess) e = mlp_backward_dev(m, batch, beta_star, s);
+      if (e != cudaSuccess) break;
+      m.adam_t += 1;
+      const float c1 = 1.f - std::pow(0.9f, (float)m.adam_t);
+      const float c2 = 1.f - std::pow(0.999f, (float)m.adam_t);
+      adam_kernel<<<1024, 256, 0, s>>>(m.mW1, m.gW1, m.am, m.av, m.nparams, lr, 0.9f, 0.999f,
+                                       1e-8f, c1, c2, m.W1, nwb);
+      e = cudaMemcpyAsync(&hloss[st], m.loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+      double acc = 0;
+      for (uint64_t st = 0; st < steps; ++st) acc += hloss[st];
+      last = acc / (double)steps;
+    }
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  float ms = 0.f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(dstates);
+  cudaFree(didx);
+  if (hloss) cudaFreeHost(hloss);
+  if (s) cudaStreamDestroy(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (final_loss) *final_loss = (float)last;
+  if (ms_out) *ms_out = ms;
+  return SK_OK;
+}
+
+}  // namespace sk
+
+extern "C" int sk_mlp_train(void* model, const uint8_t* states, uint64_t count, int epochs,
+                            int batch, float lr, float beta_star, uint64_t seed, float* final_loss,
+                            double* ms) {
+  Mlp* m = (Mlp*)model;
+  if (!m) return SK_EINVAL;
+  return sk::mlp_train_impl(*m, states, count, epochs, batch, lr, beta_star, seed, final_loss, ms);
+}

@@ -1,0 +1,69 @@
+// sk_mlp.cuh -- the move-proposal network's state and the helpers shared by
+// its training code (sk_mlp.cu) and the learned tempering chains
+// (sk_pt_learned.cu).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "sk_pt.cuh"
+
+namespace sk {
+
+constexpr int kHidden = 256;
+
+struct Mlp {
+  int variant, n, delta, bins;
+  int K1;                 // input width, padded to 128
+  int NM, NMp;            // moves, padded to 128
+  int max_batch;
+  int off[kPtMaxN + 2];   // move offsets per pair k (1-based), off[n+1] = NM
+  // parameters: bf16 copies used by the GEMMs, fp32 masters, Adam moments
+  __nv_bfloat16 *W1, *W2, *W3;
+  float *b1, *b2, *b3;
+  float *mW1, *mW2, *mW3;                    // fp32 master weights
+  float *gW1, *gW2, *gW3, *gb1, *gb2, *gb3;  // gradients
+  float *am, *av;                            // Adam moments over all parameters
+  int adam_t;
+  size_t nparams;                            // W1 | W2 | W3 | b1 | b2 | b3 (fp32 view)
+  // activations for max_batch states
+  unsigned char* slots;
+  __nv_bfloat16 *X, *H1, *H2, *dZ, *dH1, *dH2;
+  float* Z;
+  float* loss;                               // [1]
+  void* block;                               // one allocation holding all of the above
+};
+
+struct MoveTable {
+  int n, delta, NM;
+  int off[kPtMaxN + 2];   // off[k], k = 1..n+1: first move of pair k
+};
+
+// dE of moving pair k (start s_k) to start s (d = k + delta), from the bin
+// occupancies occ of the configuration: taking the pair out empties the bins
+// it was alone in; putting it back fills the empty bins it lands on.
+__device__ __forceinline__ int move_delta_e(const unsigned char* occ, int sk, int d, int s) {
+  const int out = (occ[sk] == 1) + (occ[sk + d] == 1);
+  const int o1 = occ[s] - (s == sk) - (s == sk + d);
+  const int o2 = occ[s + d] - (s + d == sk) - (s + d == sk + d);
+  return out - (o1 == 0) - (o2 == 0);
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Forward pass for B (multiple of 128) states whose start slots are in
+// m.slots: X, H1, H2 (bf16) and the logits Z (fp32, [B][NMp]).
+cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s);
+MoveTable move_table(const Mlp& m);
+
+}  // namespace sk

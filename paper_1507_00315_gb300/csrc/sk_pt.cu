@@ -1,0 +1,408 @@
+// sk_pt.cu -- the parallel-tempering kernel (Sec. 3, Algorithm 2) and its
+// host runtime: thresholds, ladder tuning, the estimator, the C ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "sk_host_common.h"
+#include "sk_pt.cuh"
+
+namespace sk {
+
+// One warp = one ladder; persistent over ladders.  Per iteration t, in the
+// order of Algorithm 2: the energy statistics of every rung (after burn-in),
+// one Metropolis move per configuration, then the exchanges of the pairs
+// (j, j+1) with j = t mod 2.
+__global__ void __launch_bounds__(128)
+    pt_kernel(PtParams p, const unsigned long long* __restrict__ tmove_g,
+              const unsigned long long* __restrict__ tswap_g, unsigned long long* hist_g,
+              unsigned long long* accm_g, unsigned long long* accs_g, unsigned char* final_slots) {
+  extern __shared__ __align__(16) unsigned char pt_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int M = p.M, n = p.n, bins = p.bins, nb = bins + 1;
+  unsigned long long* tmove = (unsigned long long*)pt_smem;            // [M][3]
+  unsigned long long* tswap = tmove + M * 3;                          // [M][bins+1]
+  for (int i = threadIdx.x; i < M * 3; i += blockDim.x) tmove[i] = tmove_g[i];
+  for (int i = threadIdx.x; i < M * nb; i += blockDim.x) tswap[i] = tswap_g[i];
+  unsigned char* wbase = pt_smem + pt_thresh_bytes(M, n) + (size_t)warp * pt_warp_bytes(M, n);
+  unsigned* hist = (unsigned*)wbase;                                   // [M][bins+1]
+  unsigned* accm = hist + M * nb;                                      // [M]
+  unsigned* accs = accm + M;                                           // [M]
+  unsigned char* slot = (unsigned char*)(accs + M);                    // [k][32], k = 1..n
+  unsigned char* occ = slot + (n + 1) * 32;                            // [b][32]
+  __syncthreads();
+  const bool active = lane < M;
+  for (int ladder = blockIdx.x * p.warps_per_block + warp; ladder < p.ladders;
+       ladder += gridDim.x * p.warps_per_block) {
+    for (int i = lane; i < M * nb; i += 32) hist[i] = 0;
+    for (int i = lane; i < M; i += 32) { accm[i] = 0; accs[i] = 0; }
+    for (int b = 0; b < bins; ++b) occ[b * 32 + lane] = 0;
+    int r = lane;           // rung (temperature) of this lane's configuration
+    int lor = lane;         // lane holding rung `lane`
+    int E = 0;
+    if (active) {
+      for (int k = 1; k <= n; ++k) {
+        const unsigned L = (unsigned)(bins - (k + p.delta));
+        const uint4 w = philox4x32_10(make_uint4((unsigned)k, (unsigned)r, (unsigned)ladder, 1u),
+                                      p.key0, p.key1);
+        const int s = (int)__umulhi(w.x, L);
+        slot[k * 32 + lane] = (unsigned char)s;
+        occ[s * 32 + lane] += 1;
+        occ[(s + k + p.delta) * 32 + lane] += 1;
+      }
+      for (int b = 0; b < bins; ++b) E += occ[b * 32 + lane] == 0;
+    }
+    __syncwarp();
+    for (unsigned long long t = 0; t < p.iters; ++t) {
+      const unsigned tt = (unsigned)t;
+      if (active) {
+        if (t >= p.burnin) hist[r * nb + E] += 1;
+        const uint4 w = philox4x32_10(make_uint4(tt, (unsigned)r, (unsigned)ladder, 2u), p.key0,
+                                      p.key1);
+        const int k = 1 + (int)__umulhi(w.x, (unsigned)n);
+        const int d = k + p.delta;
+        const int L = bins - d;
+        if (L >= 2) {
+          const int s_old = slot[k * 32 + lane];
+          int s_new = (int)__umulhi(w.y, (unsigned)(L - 1));
+          if (s_new >= s_old) ++s_new;
+          const int E0 = E;
+          unsigned char* o1 = &occ[s_old * 32 + lane];
+          unsigned char* o2 = &occ[(s_old + d) * 32 + lane];
+          unsigned char* o3 = &occ[s_new * 32 + lane];
+          unsigned char* o4 = &occ[(s_new + d) * 32 + lane];
+          if (--(*o1) == 0) ++E;
+          if (--(*o2) == 0) ++E;
+          if ((*o3)++ == 0) --E;
+          if ((*o4)++ == 0) --E;
+          const int dE = E - E0;
+          if (dE <= 0 || (unsigned long long)w.z < tmove[r * 3 + dE]) {
+            slot[k * 32 + lane] = (unsigned char)s_new;
+            accm[r] += 1;
+          } else {                                   // undo
+            if (--(*o3) == 0) ++E;
+            if (--(*o4) == 0) ++E;
+            if ((*o1)++ == 0) --E;
+            if ((*o2)++ == 0) --E;
+          }
+        }
+      }
+      // exchanges: lane j acts for rung j
+      const int Er = __shfl_sync(0xffffffffu, E, lor);
+      const int En = __shfl_down_sync(0xffffffffu, Er, 1);
+      int dec = 0;
+      if (lane + 1 < M && (lane & 1) == (int)(tt & 1u)) {
+        const uint4 w = philox4x32_10(make_uint4(tt, (unsigned)lane, (unsigned)ladder, 3u),
+                                      p.key0, p.key1);
+        const int de = Er - En;
+        dec = (de <= 0 || (unsigned long long)w.x < tswap[lane * nb + de]) ? 1 : 0;
+        if (dec) accs[lane] += 1;
+      }
+      const int lor_down = __shfl_down_sync(0xffffffffu, lor, 1);
+      const int lor_up = __shfl_up_sync(0xffffffffu, lor, 1);
+      const int dec_up = __shfl_up_sync(0xffffffffu, dec, 1);
+      lor = dec ? lor_down : ((lane > 0 && dec_up) ? lor_up : lor);
+      const int d_r = __shfl_sync(0xffffffffu, dec, r & 31);
+      const int d_rm = __shfl_sync(0xffffffffu, dec, (r + 31) & 31);
+      if (active) r = d_r ? r + 1 : ((r > 0 && d_rm) ? r - 1 : r);
+      __syncwarp();
+    }
+    // flush this ladder
+    for (int i = lane; i < M * nb; i += 32)
+      if (hist[i]) atomicAdd(&hist_g[i], (unsigned long long)hist[i]);
+    for (int i = lane; i < M; i += 32) {
+      if (accm[i]) atomicAdd(&accm_g[i], (unsigned long long)accm[i]);
+      if (accs[i]) atomicAdd(&accs_g[i], (unsigned long long)accs[i]);
+    }
+    if (final_slots && active)
+      for (int k = 1; k <= n; ++k)
+        final_slots[((size_t)ladder * M + r) * n + (k - 1)] = slot[k * 32 + lane];
+    __syncwarp();
+  }
+}
+
+}  // namespace sk
+
+// ===================================================================== host
+
+namespace sk {
+
+// ceil(p 2^32) with p = e^{-x}, x > 0; 2^32 means "always".
+unsigned long long accept_threshold(double x) {
+  const double p = std::exp(-x);
+  const double t = std::ceil(std::ldexp(p, 32));
+  if (t >= 4294967296.0) return 1ULL << 32;
+  return (unsigned long long)t;
+}
+
+namespace {
+
+int pt_check(int variant, int n, int M, const double* beta, int L) {
+  if (variant != SK_SKOLEM && variant != SK_LANGFORD) return SK_EINVAL;
+  if (n < 2 || n > kPtMaxN || M < 1 || M > kPtMaxRungs || L < 1 || !beta) return SK_EINVAL;
+  const int delta = variant == SK_LANGFORD ? 1 : 0;
+  for (int k = 1; k <= n; ++k)
+    if (2 * n - (k + delta) < 1) return SK_EINVAL;
+  for (int j = 0; j < M; ++j) {
+    if (!(beta[j] >= 0.0) || !std::isfinite(beta[j])) return SK_EINVAL;
+    if (j && beta[j] < beta[j - 1]) return SK_EINVAL;
+  }
+  return SK_OK;
+}
+
+}  // namespace
+
+// Runs L ladders for `iters` iterations; host outputs as in the header.
+int pt_run_impl(int variant, int n, int M, const double* beta, int L, uint64_t iters,
+                uint64_t burnin, uint64_t seed, uint64_t* hist, uint64_t* accm, uint64_t* accs,
+                uint8_t* final_slots, void* stream, double* kernel_ms) {
+  int st = pt_check(variant, n, M, beta, L);
+  if (st) return st;
+  if (!hist || iters > 0xffffffffULL) return SK_EINVAL;
+  st = check_device();
+  if (st) return st;
+  const int bins = 2 * n, nb = bins + 1;
+  std::vector<unsigned long long> tm((size_t)M * 3, 0), ts((size_t)M * nb, 0);
+  for (int j = 0; j < M; ++j) {
+    for (int de = 1; de <= 2; ++de) tm[j * 3 + de] = accept_threshold(beta[j] * (double)de);
+    if (j + 1 < M)
+      for (int de = 1; de <= bins; ++de)
+        ts[j * nb + de] = accept_threshold((beta[j + 1] - beta[j]) * (double)de);
+  }
+  PtParams p;
+  p.n = n;
+  p.delta = variant == SK_LANGFORD ? 1 : 0;
+  p.M = M;
+  p.bins = bins;
+  p.ladders = L;
+  p.warps_per_block = 4;
+  p.iters = iters;
+  p.burnin = burnin;
+  p.key0 = (unsigned)seed;
+  p.key1 = (unsigned)(seed >> 32);
+  const size_t smem = pt_smem_bytes(M, n, p.warps_per_block);
+  const size_t n_hist = (size_t)M * nb, n_fin = final_slots ? (size_t)L * M * n : 0;
+  const size_t bytes = (tm.size() + ts.size() + n_hist + 2 * (size_t)M) * 8 + n_fin;
+  cudaStream_t s = (cudaStream_t)stream;
+  bool own = false;
+  if (!s) {
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return SK_ECUDA;
+    own = true;
+  }
+  unsigned long long* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, bytes);
+  if (e != cudaSuccess) {
+    if (own) cudaStreamDestroy(s);
+    return cuda_status(e);
+  }
+  unsigned long long* dtm = d;
+  unsigned long long* dts = dtm + tm.size();
+  unsigned long long* dh = dts + ts.size();
+  unsigned long long* dam = dh + n_hist;
+  unsigned long long* das = dam + M;
+  unsigned char* dfin = final_slots ? (unsigned char*)(das + M) : nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaMemcpyAsync(dtm, tm.data(), tm.size() * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dts, ts.data(), ts.size() * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dh, 0, (n_hist + 2 * (size_t)M) * 8, s);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(pt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pt_kernel, 32 * p.warps_per_block, smem);
+  int grid = sms * (per_sm > 0 ? per_sm : 1);
+  const int need = (L + p.warps_per_block - 1) / p.warps_per_block;
+  if (grid > need) grid = need;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  if (e == cudaSuccess) {
+    pt_kernel<<<grid, 32 * p.warps_per_block, smem, s>>>(p, dtm, dts, dh, dam, das, dfin);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  std::vector<unsigned long long> hh(n_hist + 2 * (size_t)M);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hh.data(), dh, hh.size() * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && final_slots)
+    e = cudaMemcpyAsync(final_slots, dfin, n_fin, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  float ms = 0.f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(d);
+  if (own) cudaStreamDestroy(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (size_t i = 0; i < n_hist; ++i) hist[i] = hh[i];
+  for (int j = 0; j < M; ++j) {
+    if (accm) accm[j] = hh[n_hist + j];
+    if (accs) accs[j] = hh[n_hist + M + j];
+  }
+  if (kernel_ms) *kernel_ms = ms;
+  return SK_OK;
+}
+
+// Sec. 3: S ~ 1/2 Z(0) prod_j Ratio(j); Ratio(j) = mean of
+// e^{-(beta_{j+1} - beta_j) E} at rung j, and for the last rung
+// (beta_{M+1} = infinity) the fraction of samples with E = 0.
+double pt_estimate_from_hist(int variant, int n, int M, const double* beta, const uint64_t* hist,
+                             double* ratios) {
+  const int nb = 2 * n + 1, delta = variant == SK_LANGFORD ? 1 : 0;
+  long double logs = std::log(0.5L);
+  for (int k = 1; k <= n; ++k) logs += std::log((long double)(2 * n - (k + delta)));
+  for (int j = 0; j < M; ++j) {
+    long double tot = 0, acc = 0;
+    for (int E = 0; E < nb; ++E) {
+      const long double h = (long double)hist[j * nb + E];
+      tot += h;
+      if (j + 1 < M) acc += h * std::exp(-(long double)(beta[j + 1] - beta[j]) * E);
+      else if (E == 0) acc += h;
+    }
+    const long double rr = tot > 0 ? acc / tot : 0;
+    if (ratios) ratios[j] = (double)rr;
+    logs += std::log(rr);
+  }
+  return (double)std::exp(logs);
+}
+
+}  // namespace sk
+
+extern "C" int sk_pt_run(int variant, int n, int M, const double* beta, int L, uint64_t iters,
+                         uint64_t burnin, uint64_t seed, uint64_t* hist, uint64_t* acc_move,
+                         uint64_t* acc_swap, uint8_t* final_slots) {
+  return sk::pt_run_impl(variant, n, M, beta, L, iters, burnin, seed, hist, acc_move, acc_swap,
+                         final_slots, nullptr, nullptr);
+}
+
+namespace sk {
+
+// Pilot-tuned ladder: beta_0 = 0 and beta_{M-1} = beta_max fixed; the inner
+// temperatures are moved so that every neighbour pair has the same
+// -log(exchange acceptance) (Sec. 3 asks for acceptance >= 1/2 with few
+// temperatures); a few short pilot runs, each re-spacing the ladder along
+// the cumulative -log acceptance.
+int tune_ladder(int variant, int n, int M, double beta_max, uint64_t seed, void* stream,
+                double* beta) {
+  if (M < 2) {
+    beta[0] = 0.0;
+    return SK_OK;
+  }
+  for (int j = 0; j < M; ++j) {            // start: dense at small beta
+    const double x = (double)j / (M - 1);
+    beta[j] = beta_max * (std::exp(3.0 * x) - 1.0) / (std::exp(3.0) - 1.0);
+  }
+  const int nb = 2 * n + 1, L = 256;
+  const uint64_t iters = 4096, burn = 512;
+  std::vector<uint64_t> hist((size_t)M * nb), am(M), as(M);
+  for (int round = 0; round < 5; ++round) {
+    int st = pt_run_impl(variant, n, M, beta, L, iters, burn, seed + 7919 * (round + 1),
+                         hist.data(), am.data(), as.data(), nullptr, stream, nullptr);
+    if (st) return st;
+    std::vector<double> C(M, 0.0);
+    for (int j = 0; j + 1 < M; ++j) {
+      const double tries = (double)L * (double)((iters + ((j & 1) ? 0 : 1)) / 2);
+      double a = as[j] / tries;
+      a = std::min(std::max(a, 0.02), 0.999);
+      C[j + 1] = C[j] - std::log(a);
+    }
+    std::vector<double> nbeta(M);
+    nbeta[0] = 0.0;
+    nbeta[M - 1] = beta_max;
+    for (int k = 1; k + 1 < M; ++k) {
+      const double target = C[M - 1] * k / (M - 1);
+      int j = 0;
+      while (j + 2 < M && C[j + 1] < target) ++j;
+      const double span = C[j + 1] - C[j];
+      const double f = span > 0 ? (target - C[j]) / span : 0.0;
+      nbeta[k] = beta[j] + f * (beta[j + 1] - beta[j]);
+    }
+    for (int k = 1; k < M; ++k) nbeta[k] = std::max(nbeta[k], nbeta[k - 1]);
+    for (int k = 0; k < M; ++k) beta[k] = nbeta[k];
+  }
+  return SK_OK;
+}
+
+int pt_estimate_impl(int variant, int n, uint64_t budget, const sk_pt_opts* o, double* out,
+                     sk_pt_report* rep) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!out || budget == 0 || budget > 0xffffffffULL) return SK_EINVAL;
+  const int M = (o && o->rungs) ? o->rungs : 32;
+  const int L = (o && o->ladders) ? o->ladders : 4096;
+  const uint64_t seed = o ? o->seed : 0;
+  const double bf = (o && o->burnin_frac != 0.0) ? o->burnin_frac : 0.1;
+  const uint64_t burnin = bf < 0 ? 0 : (uint64_t)(bf * (double)budget);
+  const int proposal = o ? o->proposal : SK_PT_PLAIN;
+  if (M < 1 || M > kPtMaxRungs || L < 1 || burnin >= budget) return SK_EINVAL;
+  if (proposal != SK_PT_PLAIN && proposal != SK_PT_LEARNED) return SK_EINVAL;
+  if (variant != SK_SKOLEM && variant != SK_LANGFORD) return SK_EINVAL;
+  if (n < 2 || n > kPtMaxN) return SK_EINVAL;
+  std::vector<double> beta(M);
+  if (o && o->beta) {
+    for (int j = 0; j < M; ++j) beta[j] = o->beta[j];
+  } else {
+    const double bmax = (o && o->beta_max > 0) ? o->beta_max : 32.0;
+    int st = tune_ladder(variant, n, M, bmax, seed ^ 0x5DEECE66DULL, o ? o->stream : nullptr,
+                         beta.data());
+    if (st) return st;
+  }
+  auto t1 = std::chrono::steady_clock::now();
+  const int nb = 2 * n + 1;
+  std::vector<uint64_t> hist((size_t)M * nb), am(M), as(M);
+  double kms = 0.0;
+  int st;
+  if (proposal == SK_PT_LEARNED)
+    st = pt_learned_run(variant, n, M, beta.data(), L, budget, burnin, seed, o->model, hist.data(),
+                        am.data(), as.data(), o ? o->stream : nullptr, &kms);
+  else
+    st = pt_run_impl(variant, n, M, beta.data(), L, budget, burnin, seed, hist.data(), am.data(),
+                     as.data(), nullptr, o ? o->stream : nullptr, &kms);
+  if (st) return st;
+  double ratios[kPtMaxRungs];
+  const double est = pt_estimate_from_hist(variant, n, M, beta.data(), hist.data(), ratios);
+  *out = est;
+  if (rep) {
+    std::memset(rep, 0, sizeof(*rep));
+    rep->rungs = M;
+    rep->ladders = L;
+    rep->iterations = budget;
+    rep->burnin = burnin;
+    for (int j = 0; j < M; ++j) {
+      rep->beta[j] = beta[j];
+      rep->ratio[j] = ratios[j];
+      rep->acc_move[j] = (double)am[j] / ((double)L * (double)budget);
+      const double tries = (double)L * (double)((budget + ((j & 1) ? 0 : 1)) / 2);
+      rep->acc_swap[j] = j + 1 < M ? (double)as[j] / tries : 0.0;
+    }
+    rep->estimate = est;
+    rep->kernel_ms = kms;
+    rep->tune_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    rep->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return SK_OK;
+}
+
+}  // namespace sk
+
+extern "C" int pt_estimate(int variant, int n, uint64_t budget, double* out) {
+  return sk::pt_estimate_impl(variant, n, budget, nullptr, out, nullptr);
+}
+
+extern "C" int pt_estimate_ex(int variant, int n, uint64_t budget, const sk_pt_opts* opts,
+                              double* out, sk_pt_report* rep) {
+  return sk::pt_estimate_impl(variant, n, budget, opts, out, rep);
+}
+
+extern "C" int sk_pt_tune_ladder(int variant, int n, int rungs, double beta_max, uint64_t seed,
+                                 double* beta) {
+  if (!beta || rungs < 1 || rungs > sk::kPtMaxRungs || !(beta_max > 0)) return SK_EINVAL;
+  if (variant != SK_SKOLEM && variant != SK_LANGFORD) return SK_EINVAL;
+  if (n < 2 || n > sk::kPtMaxN) return SK_EINVAL;
+  int st = sk::check_device();
+  if (st) return st;
+  return sk::tune_ladder(variant, n, rungs, beta_max, seed, nullptr, beta);
+}

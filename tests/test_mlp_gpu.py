@@ -1,0 +1,99 @@
+"""The proposal network's BF16 tensor-core forward/backward against the FP64
+reference (oracle/mlp_ref.py) on the same bf16-rounded weights and inputs,
+training progress, and the exactness of the learned Metropolis-Hastings
+chains (they must still sample the Boltzmann weights of Sec. 3)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp_ref
+import paper_1507_00315_gb300 as sk
+from tests import seeded_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+
+def _flat(params):
+    W1, b1, W2, b2, W3, b3 = params
+    return np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3.ravel(), b3]).astype(np.float32)
+
+
+def _unflat(v, n, nm):
+    sizes = [(2 * n, 256), (256,), (256, 256), (256,), (256, nm), (nm,)]
+    out, o = [], 0
+    for s in sizes:
+        c = int(np.prod(s))
+        out.append(v[o:o + c].reshape(s).astype(np.float64))
+        o += c
+    return out
+
+
+@pytest.mark.parametrize("variant,n", [(0, 8), (1, 12), (0, 33)])
+def test_forward_matches_fp64(variant, n):
+    d = si.differences(variant, n)
+    off, nslot = mlp_ref.move_table(n, d)
+    nm = int(nslot.sum())
+    model = sk.Mlp(variant, n, 512, seed=1)
+    assert model.n_moves == nm
+    params = si.mlp_params(5, 2 * n, 256, nm)
+    params = list(params)
+    params[1], params[3], params[5] = [si.bf16_round(p) for p in (params[1], params[3], params[5])]
+    model.set_params(_flat(params))
+    slots = si.random_slots(7, 300, n, d)
+    z = model.forward(slots)
+    x = mlp_ref.occupancy(slots, n, d)
+    _, _, _, _, zr = mlp_ref.forward(x, *params)
+    err = np.abs(z - zr).max() / np.abs(zr).max()
+    assert err < 2e-2, err
+
+
+@pytest.mark.parametrize("variant,n", [(0, 8), (1, 16)])
+def test_gradients_match_fp64(variant, n):
+    d = si.differences(variant, n)
+    off, nslot = mlp_ref.move_table(n, d)
+    nm = int(nslot.sum())
+    model = sk.Mlp(variant, n, 256, seed=2)
+    params = [si.bf16_round(p) for p in si.mlp_params(11, 2 * n, 256, nm)]
+    model.set_params(_flat(params))
+    slots = si.random_slots(13, 256, n, d)
+    loss, g = model.loss_grad(slots, beta_star=2.0)
+    x = mlp_ref.occupancy(slots, n, d)
+    mask = mlp_ref.valid_mask(slots, n, d)
+    target = mlp_ref.target_distribution(slots, n, d, 2.0)
+    lr, gr = mlp_ref.loss_and_grads(x, *params, mask, target)
+    assert abs(loss - lr) / abs(lr) < 1e-2
+    got = _unflat(g, n, nm)
+    for name, a in zip(["W1", "b1", "W2", "b2", "W3", "b3"], got):
+        ref = gr[name]
+        rel = np.linalg.norm(a - ref) / max(np.linalg.norm(ref), 1e-12)
+        assert rel < 3e-2, (name, rel)
+    # round trip of the parameters
+    assert np.array_equal(model.get_params(), _flat(params))
+
+
+def test_training_lowers_the_loss():
+    n, variant = 12, 0
+    d = si.differences(variant, n)
+    res = sk.pt_run(variant, n, np.linspace(0, 6, 16), 256, 300, 0, 5, want_final=True)
+    states = res["final_slots"].reshape(-1, n)                 # 4096 states from plain PT
+    model = sk.Mlp(variant, n, 1024, seed=3)
+    l0, _ = model.loss_grad(states[:1024], 2.0)
+    l1, ms = model.train(states, epochs=30, batch=1024, lr=2e-3, beta_star=2.0, seed=1)
+    l2, _ = model.loss_grad(states[:1024], 2.0)
+    assert l2 < l0 * 0.9, (l0, l1, l2)
+
+
+@pytest.mark.parametrize("variant,n", [(0, 5), (1, 4)])
+def test_learned_chains_are_exact(variant, n):
+    beta = np.array([0.0, 0.7, 1.5, 2.6, 4.0, 6.0, 9.0, 14.0])
+    model = sk.Mlp(variant, n, 1024, seed=4)
+    res = sk.pt_run(variant, n, beta, 128, 1500, 150, 21, model=model)
+    N = oracle.simplified_energy_hist(variant, n).astype(np.float64)
+    E = np.arange(2 * n + 1)
+    for j in range(len(beta)):
+        p = N * np.exp(-beta[j] * E)
+        p /= p.sum()
+        h = res["hist"][j].astype(np.float64)
+        assert np.abs(h / h.sum() - p).max() < 0.02, (j, h / h.sum(), p)
+    est = oracle.pt_estimate_from_hist(res["hist"], beta, variant, n)
+    assert abs(est / (oracle.backtrack_count(variant, n) / 2) - 1) < 0.03

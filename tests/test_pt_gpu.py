@@ -1,0 +1,74 @@
+"""Parallel tempering on the GPU against the oracle's Algorithm 2: with the
+same Philox streams and integer acceptance thresholds the trajectories are
+identical, so energy histograms, acceptance counts and final configurations
+must match exactly; the estimator against exact counts and the exact
+partition function."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1507_00315_gb300 as sk
+from tests.conftest import read_golden
+
+pytestmark = pytest.mark.gpu
+
+TABLE6_BETA = [float(r[1]) for r in read_golden("table6_pt_s12.txt")]
+
+
+@pytest.mark.parametrize("variant,n,M,L,iters,burnin,seed", [
+    (0, 5, 6, 3, 2000, 200, 11),
+    (1, 7, 8, 2, 1500, 0, 5),
+    (0, 12, 12, 2, 3000, 300, 2017),       # Table 6's ladder
+    (0, 2, 1, 1, 100, 10, 1),              # smallest: one rung, n = 2
+    (1, 3, 32, 1, 400, 40, 9),             # 32 rungs, Langford n = 3
+    (0, 33, 32, 1, 300, 30, 3),            # largest order of the workloads
+])
+def test_trajectory_equals_oracle(variant, n, M, L, iters, burnin, seed):
+    beta = TABLE6_BETA if M == 12 else list(np.linspace(0.0, 8.0, M) ** 1.3)
+    got = sk.pt_run(variant, n, beta, L, iters, burnin, seed, want_final=True)
+    want = oracle.pt_run(variant, n, beta, L, iters, burnin, seed, want_final=True)
+    assert np.array_equal(got["hist"], want["hist"])
+    assert np.array_equal(got["acc_move"], want["acc_move"])
+    assert np.array_equal(got["acc_swap"], want["acc_swap"])
+    assert np.array_equal(got["final_slots"], want["final_slots"])
+
+
+@pytest.mark.parametrize("variant,n", [(0, 4), (0, 5), (1, 4)])
+def test_ratios_against_exact_partition_function(variant, n):
+    beta = np.array([0.0, 0.5, 1.0, 1.6, 2.4, 3.5, 5.0, 8.0])
+    res = sk.pt_run(variant, n, beta, 512, 4000, 400, 77)
+    N = oracle.simplified_energy_hist(variant, n).astype(np.float64)
+    E = np.arange(2 * n + 1)
+    for j in range(len(beta)):
+        p = N * np.exp(-beta[j] * E)
+        p /= p.sum()
+        h = res["hist"][j].astype(np.float64)
+        assert np.abs(h / h.sum() - p).max() < 0.01, j
+    est = oracle.pt_estimate_from_hist(res["hist"], beta, variant, n)
+    assert abs(est / (oracle.backtrack_count(variant, n) / 2) - 1) < 0.01
+
+
+def test_pt_estimate_small_orders(skolem_table, langford_table):
+    for variant, n, table in ((0, 8, skolem_table), (1, 8, langford_table), (0, 9, skolem_table)):
+        est, rep = sk.pt_estimate(variant, n, 20000, ladders=1024, seed=1)
+        assert abs(est / table[n] - 1) < 0.01, (variant, n, est, rep["acc_swap"])
+
+
+def test_pt_estimate_n12_within_one_percent(skolem_table):
+    est, rep = sk.pt_estimate(0, 12, 40000, ladders=2048, seed=3)
+    assert abs(est / skolem_table[12] - 1) < 0.01, (est, rep["acc_swap"])
+    assert rep["beta"][0] == 0.0 and abs(rep["beta"][-1] - 32.0) < 1e-9
+
+
+def test_tuned_ladder_shape():
+    b = sk.tune_ladder(0, 16, 32, 32.0, 0)
+    assert b[0] == 0.0 and abs(b[-1] - 32.0) < 1e-12 and np.all(np.diff(b) >= 0)
+
+
+def test_pt_invalid():
+    with pytest.raises(sk.SkolemError):
+        sk.pt_estimate(2, 8, 1000)                   # hooked: not a tempering variant
+    with pytest.raises(sk.SkolemError):
+        sk.pt_run(0, 8, [1.0, 0.5], 1, 10, 0, 0)     # decreasing ladder
