@@ -85,15 +85,16 @@ def test_training_lowers_the_loss():
 
 @pytest.mark.parametrize("variant,n", [(0, 5), (1, 4)])
 def test_learned_chains_are_exact(variant, n):
+    # an untrained network: a poor proposal, so long equilibrated runs
     beta = np.array([0.0, 0.7, 1.5, 2.6, 4.0, 6.0, 9.0, 14.0])
-    model = sk.Mlp(variant, n, 1024, seed=4)
-    res = sk.pt_run(variant, n, beta, 128, 1500, 150, 21, model=model)
+    model = sk.Mlp(variant, n, 8192, seed=4)
+    res = sk.pt_run(variant, n, beta, 1024, 20000, 10000, 21, model=model)
     N = oracle.simplified_energy_hist(variant, n).astype(np.float64)
     E = np.arange(2 * n + 1)
     for j in range(len(beta)):
         p = N * np.exp(-beta[j] * E)
         p /= p.sum()
         h = res["hist"][j].astype(np.float64)
-        assert np.abs(h / h.sum() - p).max() < 0.02, (j, h / h.sum(), p)
+        assert np.abs(h / h.sum() - p).max() < 0.01, (j, h / h.sum(), p)
     est = oracle.pt_estimate_from_hist(res["hist"], beta, variant, n)
-    assert abs(est / (oracle.backtrack_count(variant, n) / 2) - 1) < 0.03
+    assert abs(est / (oracle.backtrack_count(variant, n) / 2) - 1) < 0.02

@@ -38,7 +38,7 @@ def test_trajectory_equals_oracle(variant, n, M, L, iters, burnin, seed):
 @pytest.mark.parametrize("variant,n", [(0, 4), (0, 5), (1, 4)])
 def test_ratios_against_exact_partition_function(variant, n):
     beta = np.array([0.0, 0.5, 1.0, 1.6, 2.4, 3.5, 5.0, 8.0])
-    res = sk.pt_run(variant, n, beta, 512, 4000, 400, 77)
+    res = sk.pt_run(variant, n, beta, 4096, 4000, 400, 77)
     N = oracle.simplified_energy_hist(variant, n).astype(np.float64)
     E = np.arange(2 * n + 1)
     for j in range(len(beta)):
@@ -57,7 +57,10 @@ def test_pt_estimate_small_orders(skolem_table, langford_table):
 
 
 def test_pt_estimate_n12_within_one_percent(skolem_table):
-    est, rep = sk.pt_estimate(0, 12, 40000, ladders=2048, seed=3)
+    # Algorithm 2 starts from random configurations; at n = 12 the low
+    # temperatures need ~1e5 iterations to forget them (40k: -5 %, 160k:
+    # -0.3 %, 640k: +0.1 % measured), so the budget is 320k iterations
+    est, rep = sk.pt_estimate(0, 12, 320000, ladders=1024, seed=3)
     assert abs(est / skolem_table[12] - 1) < 0.01, (est, rep["acc_swap"])
     assert rep["beta"][0] == 0.0 and abs(rep["beta"][-1] - 32.0) < 1e-9
 
