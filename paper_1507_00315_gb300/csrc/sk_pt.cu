@@ -17,24 +17,21 @@ namespace sk {
 // order of Algorithm 2: the energy statistics of every rung (after burn-in),
 // one Metropolis move per configuration, then the exchanges of the pairs
 // (j, j+1) with j = t mod 2.
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 7)
     pt_kernel(PtParams p, const unsigned long long* __restrict__ tmove_g,
               const unsigned long long* __restrict__ tswap_g, unsigned long long* hist_g,
               unsigned long long* accm_g, unsigned long long* accs_g, unsigned char* final_slots) {
   extern __shared__ __align__(16) unsigned char pt_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int M = p.M, n = p.n, bins = p.bins, nb = bins + 1;
-  unsigned long long* tmove = (unsigned long long*)pt_smem;            // [M][3]
-  unsigned long long* tswap = tmove + M * 3;                          // [M][bins+1]
-  for (int i = threadIdx.x; i < M * 3; i += blockDim.x) tmove[i] = tmove_g[i];
-  for (int i = threadIdx.x; i < M * nb; i += blockDim.x) tswap[i] = tswap_g[i];
-  unsigned char* wbase = pt_smem + pt_thresh_bytes(M, n) + (size_t)warp * pt_warp_bytes(M, n);
-  unsigned* hist = (unsigned*)wbase;                                   // [M][bins+1]
-  unsigned* accm = hist + M * nb;                                      // [M]
+  const unsigned long long* tmove = tmove_g;                           // [M][3]
+  const unsigned long long* tswap = tswap_g;                           // [M][bins+1]
+  unsigned char* wbase = pt_smem + (size_t)warp * pt_warp_bytes(M, n);
+  unsigned short* hist = (unsigned short*)wbase;                       // [M][bins+1]
+  unsigned* accm = (unsigned*)(wbase + ((size_t)M * nb * 2 + 15) / 16 * 16);   // [M]
   unsigned* accs = accm + M;                                           // [M]
   unsigned char* slot = (unsigned char*)(accs + M);                    // [k][32], k = 1..n
   unsigned char* occ = slot + (n + 1) * 32;                            // [b][32]
-  __syncthreads();
   const bool active = lane < M;
   for (int ladder = blockIdx.x * p.warps_per_block + warp; ladder < p.ladders;
        ladder += gridDim.x * p.warps_per_block) {
@@ -59,6 +56,12 @@ __global__ void __launch_bounds__(128)
     __syncwarp();
     for (unsigned long long t = 0; t < p.iters; ++t) {
       const unsigned tt = (unsigned)t;
+      if ((tt & (kPtFlush - 1)) == 0 && t > 0) {       // 16-bit counters: flush
+        __syncwarp();
+        for (int i = lane; i < M * nb; i += 32)
+          if (hist[i]) { atomicAdd(&hist_g[i], (unsigned long long)hist[i]); hist[i] = 0; }
+        __syncwarp();
+      }
       if (active) {
         if (t >= p.burnin) hist[r * nb + E] += 1;
         const uint4 w = philox4x32_10(make_uint4(tt, (unsigned)r, (unsigned)ladder, 2u), p.key0,
@@ -80,7 +83,7 @@ __global__ void __launch_bounds__(128)
           if ((*o3)++ == 0) --E;
           if ((*o4)++ == 0) --E;
           const int dE = E - E0;
-          if (dE <= 0 || (unsigned long long)w.z < tmove[r * 3 + dE]) {
+          if (dE <= 0 || (unsigned long long)w.z < __ldg(&tmove[r * 3 + dE])) {
             slot[k * 32 + lane] = (unsigned char)s_new;
             accm[r] += 1;
           } else {                                   // undo
@@ -99,7 +102,7 @@ __global__ void __launch_bounds__(128)
         const uint4 w = philox4x32_10(make_uint4(tt, (unsigned)lane, (unsigned)ladder, 3u),
                                       p.key0, p.key1);
         const int de = Er - En;
-        dec = (de <= 0 || (unsigned long long)w.x < tswap[lane * nb + de]) ? 1 : 0;
+        dec = (de <= 0 || (unsigned long long)w.x < __ldg(&tswap[lane * nb + de])) ? 1 : 0;
         if (dec) accs[lane] += 1;
       }
       const int lor_down = __shfl_down_sync(0xffffffffu, lor, 1);
@@ -112,6 +115,7 @@ __global__ void __launch_bounds__(128)
       __syncwarp();
     }
     // flush this ladder
+    __syncwarp();
     for (int i = lane; i < M * nb; i += 32)
       if (hist[i]) atomicAdd(&hist_g[i], (unsigned long long)hist[i]);
     for (int i = lane; i < M; i += 32) {

@@ -44,19 +44,19 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1
   return c;
 }
 
-// Shared-memory layout of one block: thresholds, then per warp the histogram
-// (M x (bins+1) u32), accepted moves and exchanges (M u32 each), start slots
-// ([k][lane] bytes) and bin occupancies ([b][lane] bytes).
+// Shared-memory layout of one warp: the energy histogram (M x (bins+1)
+// 16-bit counters, flushed to global memory every kPtFlush iterations),
+// accepted moves and exchanges (M u32 each), start slots ([k][lane] bytes)
+// and bin occupancies ([b][lane] bytes).  The acceptance thresholds stay in
+// global memory (L1-cached), so about 28 warps fit on an SM.
+constexpr unsigned kPtFlush = 32768;
 __host__ __device__ inline size_t pt_warp_bytes(int M, int n) {
-  const size_t hist = (size_t)M * (2 * n + 1) * 4 + 2 * (size_t)M * 4;
+  const size_t hist = ((size_t)M * (2 * n + 1) * 2 + 15) / 16 * 16 + 2 * (size_t)M * 4;
   const size_t st = (size_t)(n + 1) * 32 + (size_t)(2 * n) * 32;
   return (hist + st + 15) / 16 * 16;
 }
-__host__ __device__ inline size_t pt_thresh_bytes(int M, int n) {
-  return ((size_t)M * 3 + (size_t)M * (2 * n + 1)) * 8;
-}
 __host__ __device__ inline size_t pt_smem_bytes(int M, int n, int wpb) {
-  return pt_thresh_bytes(M, n) + (size_t)wpb * pt_warp_bytes(M, n);
+  return (size_t)wpb * pt_warp_bytes(M, n);
 }
 
 // Host helpers shared by the plain and the learned chains (sk_pt.cu).
