@@ -277,7 +277,7 @@ def run_pt_bench(args, sk, sh):
     for v, n in cases:
         exact = (EXACT_S if v == 0 else EXACT_L)[n]
         rows = []
-        for budget in args.pt_budgets:
+        for budget in sorted(set(args.pt_budgets) | set(args.pt_learned_budgets)):
             est, rep = sk.pt_estimate(v, n, budget, ladders=4096, seed=budget, stream=sh)
             rows.append({"proposal": "plain", "iterations": budget, "estimate": est,
                          "rel_error": est / exact - 1, "gpu_ms": rep["kernel_ms"],
@@ -301,7 +301,13 @@ def run_pt_bench(args, sk, sh):
                          "train_samples": int(states.shape[0])})
         model.close()
         out[f"{'SL'[v]}({n})"] = rows
+    summary = {}
+    for case, rows in out.items():
+        for prop in ("plain", "learned"):
+            ok = [r for r in rows if r["proposal"] == prop and abs(r["rel_error"]) < 0.01]
+            summary[f"{case} {prop}: GPU ms to |error| < 1%"] = min((r["gpu_ms"] for r in ok), default=None)
     return {"metric": "PT relative error vs GPU time, learned vs plain proposal",
+            "summary": summary,
             "config": {"workload": "32 temperatures x 4096 ladders, Skolem / Langford n=16..24",
                        "training": f"{args.pt_samples} plain-PT states, 1 epoch, Adam 1e-3"},
             "unit": "relative error", "results": out}
