@@ -281,6 +281,12 @@ int sk_mlp_loss_grad(void *model, const uint8_t *slots, int B, float beta_star, 
  * time (both may be NULL). */
 int sk_mlp_train(void *model, const uint8_t *states, uint64_t count, int epochs, int batch,
                  float lr, float beta_star, uint64_t seed, float *final_loss, double *ms);
+/* Selects the forward GEMM path of a model: 1 (default) the 5th-generation
+ * tensor cores (tcgen05, accumulators in tensor memory), 0 warp-level
+ * mma.sync.  sk_mlp_check returns SK_ETIMEOUT if a tensor-core wait of the
+ * model ever gave up (the results of that call are then invalid). */
+int sk_mlp_set_gemm(void *model, int use_tensor_memory_path);
+int sk_mlp_check(void *model);
 /* The learned tempering run behind pt_estimate_ex with SK_PT_LEARNED, with
  * the outputs of sk_pt_run (no final states).  Needs a model of the same
  * (variant, n) whose max_batch >= L * M rounded up to 128. */

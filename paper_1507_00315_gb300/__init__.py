@@ -196,6 +196,8 @@ def lib():
         L.sk_mlp_get_params.argtypes = [vp, vp]
         L.sk_mlp_forward.argtypes = [vp, vp, ctypes.c_int, vp]
         L.sk_mlp_loss_grad.argtypes = [vp, vp, ctypes.c_int, ctypes.c_float, vp, vp]
+        L.sk_mlp_set_gemm.argtypes = [vp, ctypes.c_int]
+        L.sk_mlp_check.argtypes = [vp]
         L.sk_mlp_train.argtypes = [vp, vp, u64, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                    ctypes.c_float, u64, vp, vp]
         L.sk_int32_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -436,6 +438,17 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+    def set_gemm(self, tensor_memory: bool):
+        """True: tcgen05 forward (default); False: mma.sync forward."""
+        st = lib().sk_mlp_set_gemm(self.handle, int(bool(tensor_memory)))
+        if st != SK_OK:
+            raise SkolemError(st, "sk_mlp_set_gemm")
+
+    def check(self):
+        st = lib().sk_mlp_check(self.handle)
+        if st != SK_OK:
+            raise SkolemError(st, "sk_mlp_check")
 
     def set_params(self, flat):
         np = _np()

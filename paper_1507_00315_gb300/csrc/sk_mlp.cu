@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "sk_gemm.cuh"
+#include "sk_gemm_tc.cuh"
 #include "sk_host_common.h"
 #include "sk_mlp.cuh"
 
@@ -157,10 +158,66 @@ MoveTable move_table(const Mlp& m) {
   return t;
 }
 
+// out[c][r] = in[r][c] for a rows x cols bf16 matrix.
+__global__ void transpose_bf16_kernel(const __nv_bfloat16* in, int rows, int cols,
+                                      __nv_bfloat16* out) {
+  __shared__ __nv_bfloat16 t[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) t[i][threadIdx.x] = in[(size_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[(size_t)c * rows + r] = t[threadIdx.x][i];
+  }
+}
+
+cudaError_t refresh_transposed(Mlp& m, cudaStream_t s) {
+  dim3 b(32, 8);
+  transpose_bf16_kernel<<<dim3(kHidden / 32, m.K1 / 32), b, 0, s>>>(m.W1, m.K1, kHidden, m.W1t);
+  transpose_bf16_kernel<<<dim3(kHidden / 32, kHidden / 32), b, 0, s>>>(m.W2, kHidden, kHidden, m.W2t);
+  transpose_bf16_kernel<<<dim3(m.NMp / 32, kHidden / 32), b, 0, s>>>(m.W3, kHidden, m.NMp, m.W3t);
+  m.wt_dirty = 0;
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_tc(const TcGemmArgs& g, cudaStream_t s) {
+  if (g.M % kTcBM || g.N % kTcBN || g.K % kTcBK) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kTcSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  gemm_tc_kernel<<<dim3(g.N / kTcBN, g.M / kTcBM), 128, kTcSmem, s>>>(g);
+  return cudaGetLastError();
+}
+
 // Forward pass for B (multiple of 128) states whose slots are already in
 // m.slots: X, H1, H2 (bf16) and Z (fp32 logits).
 cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s) {
   mlp_inputs_kernel<<<(B + 127) / 128, 128, 0, s>>>(m.slots, B, m.n, m.delta, m.K1, m.X);
+  if (m.use_tc) {
+    cudaError_t e = cudaSuccess;
+    if (m.wt_dirty) e = refresh_transposed(m, s);
+    if (e != cudaSuccess) return e;
+    TcGemmArgs t;
+    std::memset(&t, 0, sizeof(t));
+    t.M = B; t.N = kHidden; t.K = m.K1; t.A = m.X; t.lda = m.K1; t.Bt = m.W1t; t.ldb = m.K1;
+    t.C = m.H1; t.ldc = kHidden; t.bias = m.b1; t.relu_bf16 = 1; t.err = m.tc_err;
+    e = gemm_tc(t, s);
+    if (e != cudaSuccess) return e;
+    t.K = kHidden; t.A = m.H1; t.lda = kHidden; t.Bt = m.W2t; t.ldb = kHidden; t.C = m.H2;
+    t.bias = m.b2;
+    e = gemm_tc(t, s);
+    if (e != cudaSuccess) return e;
+    t.N = m.NMp; t.A = m.H2; t.Bt = m.W3t; t.ldb = kHidden; t.C = m.Z; t.ldc = m.NMp;
+    t.bias = m.b3; t.relu_bf16 = 0;
+    return gemm_tc(t, s);
+  }
   GemmArgs g;
   std::memset(&g, 0, sizeof(g));
   g.M = B; g.N = kHidden; g.K = m.K1; g.A = m.X; g.lda = m.K1; g.B = m.W1; g.ldb = kHidden;
@@ -257,7 +314,7 @@ int mlp_create(int variant, int n, int max_batch, uint64_t seed, Mlp** out) {
   m->off[1] = 0;
   for (int k = 1; k <= n; ++k) m->off[k + 1] = m->off[k] + (2 * n - (k + m->delta));
   m->NM = m->off[n + 1];
-  m->NMp = (m->NM + 127) / 128 * 128;
+  m->NMp = (m->NM + 255) / 256 * 256;
   const size_t w1 = (size_t)m->K1 * kHidden, w2 = (size_t)kHidden * kHidden,
                w3 = (size_t)kHidden * m->NMp;
   m->nparams = w1 + w2 + w3 + 2 * kHidden + m->NMp;
@@ -277,6 +334,8 @@ int mlp_create(int variant, int n, int max_batch, uint64_t seed, Mlp** out) {
   const size_t o_dz = off; off = al256(off + B * m->NMp * 2);
   const size_t o_z = off; off = al256(off + B * m->NMp * 4);
   const size_t o_loss = off; off = al256(off + 4);
+  const size_t o_wt = off; off = al256(off + (w1 + w2 + w3) * 2);
+  const size_t o_err = off; off = al256(off + 4);
   char* p = nullptr;
   if (cudaMalloc(&p, off) != cudaSuccess) {
     delete m;
@@ -302,6 +361,11 @@ int mlp_create(int variant, int n, int max_batch, uint64_t seed, Mlp** out) {
   m->dZ = (__nv_bfloat16*)(p + o_dz);
   m->Z = (float*)(p + o_z);
   m->loss = (float*)(p + o_loss);
+  __nv_bfloat16* wt = (__nv_bfloat16*)(p + o_wt);
+  m->W1t = wt; m->W2t = wt + w1; m->W3t = wt + w1 + w2;
+  m->tc_err = (unsigned*)(p + o_err);
+  m->use_tc = 1;
+  m->wt_dirty = 1;
   // He-normal initial weights (input rows beyond 2n and move columns beyond
   // NM stay zero), zero biases
   std::vector<float> h(m->nparams, 0.f);
@@ -317,6 +381,7 @@ int mlp_create(int variant, int n, int max_batch, uint64_t seed, Mlp** out) {
   cudaError_t e = cudaMemcpy(par, h.data(), m->nparams * 4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->am, 0, m->nparams * 4);
   if (e == cudaSuccess) e = cudaMemset(m->av, 0, m->nparams * 4);
+  if (e == cudaSuccess) e = cudaMemset(m->tc_err, 0, 4);
   if (e == cudaSuccess) {
     f32_to_bf16_kernel<<<256, 256>>>(par, wb, w1 + w2 + w3);
     e = cudaDeviceSynchronize();
@@ -416,6 +481,7 @@ extern "C" int sk_mlp_set_params(void* model, const float* params) {
     e = cudaDeviceSynchronize();
   }
   m->adam_t = 0;
+  m->wt_dirty = 1;
   return sk::cuda_status(e);
 }
 
@@ -438,7 +504,11 @@ extern "C" int sk_mlp_forward(void* model, const uint8_t* slots, int B, float* l
   if (e == cudaSuccess)
     e = cudaMemcpy2D(logits, (size_t)m->NM * 4, m->Z, (size_t)m->NMp * 4, (size_t)m->NM * 4, B,
                      cudaMemcpyDeviceToHost);
-  return sk::cuda_status(e);
+  if (e != cudaSuccess) return sk::cuda_status(e);
+  unsigned err = 0;
+  e = cudaMemcpy(&err, m->tc_err, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return sk::cuda_status(e);
+  return err ? SK_ETIMEOUT : SK_OK;
 }
 
 extern "C" int sk_mlp_loss_grad(void* model, const uint8_t* slots, int B, float beta_star,
@@ -503,6 +573,7 @@ int mlp_train_impl(Mlp& m, const uint8_t* states, uint64_t count, int epochs, in
       const float c2 = 1.f - std::pow(0.999f, (float)m.adam_t);
       adam_kernel<<<1024, 256, 0, s>>>(m.mW1, m.gW1, m.am, m.av, m.nparams, lr, 0.9f, 0.999f,
                                        1e-8f, c1, c2, m.W1, nwb);
+      m.wt_dirty = 1;
       e = cudaMemcpyAsync(&hloss[st], m.loss, sizeof(float), cudaMemcpyDeviceToHost, s);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -536,4 +607,21 @@ extern "C" int sk_mlp_train(void* model, const uint8_t* states, uint64_t count, 
   Mlp* m = (Mlp*)model;
   if (!m) return SK_EINVAL;
   return sk::mlp_train_impl(*m, states, count, epochs, batch, lr, beta_star, seed, final_loss, ms);
+}
+
+// The tcgen05 forward records an error word when a bounded wait gives up.
+extern "C" int sk_mlp_set_gemm(void* model, int use_tensor_memory_path) {
+  Mlp* m = (Mlp*)model;
+  if (!m) return SK_EINVAL;
+  m->use_tc = use_tensor_memory_path ? 1 : 0;
+  return SK_OK;
+}
+
+extern "C" int sk_mlp_check(void* model) {
+  Mlp* m = (Mlp*)model;
+  if (!m) return SK_EINVAL;
+  unsigned err = 0;
+  cudaError_t e = cudaMemcpy(&err, m->tc_err, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return sk::cuda_status(e);
+  return err ? SK_ETIMEOUT : SK_OK;
 }

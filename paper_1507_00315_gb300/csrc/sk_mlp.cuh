@@ -16,7 +16,7 @@ constexpr int kHidden = 256;
 struct Mlp {
   int variant, n, delta, bins;
   int K1;                 // input width, padded to 128
-  int NM, NMp;            // moves, padded to 128
+  int NM, NMp;            // moves, padded to 256
   int max_batch;
   int off[kPtMaxN + 2];   // move offsets per pair k (1-based), off[n+1] = NM
   // parameters: bf16 copies used by the GEMMs, fp32 masters, Adam moments
@@ -30,6 +30,11 @@ struct Mlp {
   // activations for max_batch states
   unsigned char* slots;
   __nv_bfloat16 *X, *H1, *H2, *dZ, *dH1, *dH2;
+  // K-major (transposed) bf16 weights for the tcgen05 forward: [out][in]
+  __nv_bfloat16 *W1t, *W2t, *W3t;
+  int use_tc;                                // 1: forward on tcgen05 (default)
+  int wt_dirty;                              // transposed copies need a refresh
+  unsigned* tc_err;                          // error word of the tcgen05 GEMM
   float* Z;
   float* loss;                               // [1]
   void* block;                               // one allocation holding all of the above

@@ -28,12 +28,14 @@ def _unflat(v, n, nm):
     return out
 
 
+@pytest.mark.parametrize("tensor_memory", [True, False])
 @pytest.mark.parametrize("variant,n", [(0, 8), (1, 12), (0, 33)])
-def test_forward_matches_fp64(variant, n):
+def test_forward_matches_fp64(variant, n, tensor_memory):
     d = si.differences(variant, n)
     off, nslot = mlp_ref.move_table(n, d)
     nm = int(nslot.sum())
     model = sk.Mlp(variant, n, 512, seed=1)
+    model.set_gemm(tensor_memory)
     assert model.n_moves == nm
     params = si.mlp_params(5, 2 * n, 256, nm)
     params = list(params)
@@ -41,6 +43,7 @@ def test_forward_matches_fp64(variant, n):
     model.set_params(_flat(params))
     slots = si.random_slots(7, 300, n, d)
     z = model.forward(slots)
+    model.check()
     x = mlp_ref.occupancy(slots, n, d)
     _, _, _, _, zr = mlp_ref.forward(x, *params)
     err = np.abs(z - zr).max() / np.abs(zr).max()
@@ -98,3 +101,18 @@ def test_learned_chains_are_exact(variant, n):
         assert np.abs(h / h.sum() - p).max() < 0.01, (j, h / h.sum(), p)
     est = oracle.pt_estimate_from_hist(res["hist"], beta, variant, n)
     assert abs(est / (oracle.backtrack_count(variant, n) / 2) - 1) < 0.02
+
+
+def test_tensor_memory_and_mma_sync_paths_agree():
+    # the two forward GEMM paths see the same bf16 operands; their fp32 sums
+    # differ only in accumulation order
+    n, variant = 20, 1
+    d = si.differences(variant, n)
+    model = sk.Mlp(variant, n, 4096, seed=6)
+    slots = si.random_slots(8, 4096, n, d)
+    model.set_gemm(True)
+    a = model.forward(slots)
+    model.check()
+    model.set_gemm(False)
+    b = model.forward(slots)
+    assert np.abs(a - b).max() <= 1e-2 * np.abs(b).max()
