@@ -69,19 +69,20 @@ def group_bits(delta, n):
 
 
 def alg_ops_per_term(variant, n, nprimes=3):
-    """INT32 operations the exact-limb form needs per term: n correlation
-    adds; n - g int32 multiplies inside the groups; g absolute values; one
-    32x32 multiply per limb of each partial product after the first group;
-    the sign-masked add of the product (PL limbs) into the accumulator (AL
-    limbs).  The moduli enter once per work item, not per term."""
+    """32-bit integer operations one term of Lemma 2.1 needs, whatever form
+    the kernel takes: n correlation updates (one add each); the exact product
+    of the n factors -- n - g int32 multiplies inside the g int32 groups
+    (bound < 2^31 each, greedy), then, per further group, one 32x32->64
+    multiply per 32-bit word of the running product (counted as two
+    operations: it yields two words); and one add per 32-bit word of the
+    signed accumulate.  The moduli enter once per work item, not per term."""
     delta = 1 if variant == 1 else 0
     bits = group_bits(delta, n)
     g = len(bits)
-    limbs = [max(1, (b + 31) // 32) for b in bits]
-    muls = sum(limbs[1:])
-    PL = limbs[-1]
-    AL = (bits[-1] + 1 + 26 + 31) // 32
-    return n + (n - g) + g + muls + PL + AL
+    words = [max(1, (b + 31) // 32) for b in bits]
+    wide = sum(words[:-1])
+    acc = (bits[-1] + 1 + 31) // 32
+    return n + (n - g) + 2 * wide + acc
 
 
 # ------------------------------------------------------------------ clocks

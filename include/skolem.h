@@ -59,10 +59,10 @@ enum { SK_COUNT_REFLECTIONS_IDENTIFIED = 0, SK_COUNT_ALL = 1 };
 #define SK_MAX_N 28        /* largest n with a compiled exact kernel */
 
 /* Arithmetic form of the term products (both give identical residues).
- * SK_ARITH_LIMBS: every term's product is formed exactly in 32-bit limbs
- * (|prod c_k| <= prod_k L_k, L_k = number of pairs at distance d_k) and added
- * into an exact accumulator; each work item's sum is reduced modulo the
- * primes once.  SK_ARITH_MONTGOMERY: every term's product is formed modulo
+ * SK_ARITH_LIMBS: every term's product is formed exactly, as signed
+ * radix-2^31 digits (|prod c_k| <= prod_k L_k, L_k = number of pairs at
+ * distance d_k), and added into exact 64-bit words per digit; each work
+ * item's sum is reduced modulo the primes once.  SK_ARITH_MONTGOMERY: every term's product is formed modulo
  * each prime by signed Montgomery steps (R = 2^32); compiled for three
  * moduli only (nprimes = 3). */
 enum { SK_ARITH_LIMBS = 0, SK_ARITH_MONTGOMERY = 1 };

@@ -119,7 +119,7 @@ int batch_primes(const sk_batch_opts* o, int* k, uint64_t* pv, Primes* P) {
 
 int delta_of(int variant) { return variant == SK_LANGFORD ? 1 : 0; }
 
-// Times the exact-limb kernel of one (variant, n) on the first items (a fixed
+// Times the exact-form kernel of one (variant, n) on the first items (a fixed
 // number of terms for every candidate) and keeps the fastest configuration.
 int tune_impl(int variant, int n, const sk_batch_opts* o, sk_tune_result* out) {
   if (variant < SK_SKOLEM || variant > SK_HOOKED || n < 1 || n > kMaxN || !out) return SK_EINVAL;

@@ -23,7 +23,7 @@ struct BatchJobDev {
 };
 
 // Residues of one item of a job (zero for an item past the job's end); the
-// walk itself is the exact-limb item function of the single-job kernel.
+// walk itself is the exact-form item function of the single-job kernel.
 template <int DELTA, int N>
 __device__ __forceinline__ Res4 batch_item_impl(const BatchJobDev* job, const Primes* P,
                                                 int nprimes, unsigned long long item,

@@ -22,16 +22,20 @@
 // the only run-time operand is the outer neighbour, held as w_i = 2 x_i
 // (0 for an absent position), so each c_k update is one three-input add.
 //
-// Product.  |c_k| <= L_k = number of pairs (a, a+d_k) in the span.  The c_k
-// are multiplied in int32 in groups whose bound stays below 2^31; the first two
-// groups form an exact int64 head (< 2^62); each further group enters through
-// one signed Montgomery step modulo each 62-bit prime (Sec. 2.2: residues
-// modulo co-primes, rebuilt by the Chinese remainder theorem on the host).  A
-// Montgomery step with R = 2^32 on a in (-2^62, 2^62) and b in (-2^31, 2^31)
-// returns (a b + m p) / 2^32 with m chosen so the division is exact; the result
-// is congruent to a b R^{-1} and stays inside (-2^62, 2^62).  Every term of a
-// problem takes the same number of steps, so the sum carries one known factor
-// R^{-(g-2)} that the host removes.
+// Product.  |c_k| <= L_k = number of pairs (a, a+d_k) in the span, so the c_k
+// are multiplied in int32 groups whose bound stays below 2^31.  Two forms of
+// the rest give the same residues (Sec. 2.2: residues modulo co-primes,
+// rebuilt by the Chinese remainder theorem on the host):
+//   exact digit form (default): the groups are combined exactly in signed
+//     radix-2^31 digits and summed in 64-bit words per digit; the item sum is
+//     reduced modulo each 62-bit prime once per item.
+//   Montgomery form: the first two groups form an exact int64 head (< 2^62);
+//     each further group enters through one signed Montgomery step modulo
+//     each prime.  A step with R = 2^32 on a in (-2^62, 2^62) and b in
+//     (-2^31, 2^31) returns (a b + m p) / 2^32 with m chosen so the division
+//     is exact; the result is congruent to a b R^{-1} and stays inside
+//     (-2^62, 2^62).  Every term takes the same number of steps, so the sum
+//     carries one known factor R^{-(g-2)} that the host removes.
 #pragma once
 #include <cstdint>
 
@@ -196,20 +200,31 @@ __device__ __forceinline__ void inner_update(int (&c)[N], const int (&near)[near
   }
 }
 
+// Byte loads and stores of the shared copy of w (32-bit shared addresses, so
+// they stay shared-memory accesses inside the non-inlined item function).
+__device__ __forceinline__ int lds_s8(unsigned a) {
+  int v;
+  asm volatile("ld.shared.s8 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts_s8(unsigned a, int v) {
+  asm volatile("st.shared.s8 [%0], %1;" ::"r"(a), "r"(v));
+}
+
 // Outer flip of bit J (inner bits all +1 at this point, and +2 in ws).
-// ws points at this thread's entry for position 0.
+// wsa: shared-memory address of this thread's entry for position 0.
 template <int DELTA, int N, int U>
 __device__ __forceinline__ void outer_flip(int J, int (&c)[N], int (&near)[near_count(DELTA, N)],
-                                           signed char* ws) {
-  signed char* wj = ws + J * kWsStride;
-  const int sJ = (int)(*wj) >> 1;
+                                           unsigned wsa) {
+  const unsigned wj = wsa + (unsigned)J * kWsStride;
+  const int sJ = lds_s8(wj) >> 1;
 #pragma unroll
   for (int k = 1; k <= N; ++k) {
     const int d = k + DELTA;
-    const int t = (int)wj[-d * kWsStride] + (int)wj[d * kWsStride];
+    const int t = lds_s8(wj - d * kWsStride) + lds_s8(wj + d * kWsStride);
     c[k - 1] -= sJ * t;
   }
-  *wj = (signed char)(-2 * sJ);
+  sts_s8(wj, -2 * sJ);
   // keep the register window in step with ws
 #define SK_NCASE(I)                                                              \
   case I:                                                                        \
@@ -314,168 +329,443 @@ struct MontAcc {
   }
 };
 
-// ------------------------------------------------------------ exact limb form
+// ------------------------------------------------------------ exact digit form
 
-// Compile-time bit lengths of the products of the c_k bounds L_k, group by
-// group, computed in 32-bit limbs.
-struct BoundInfo {
-  int bits[kMaxN + 1];   // bit length of prod of bounds of groups 0..j
+// Signed-digit form of the exact product.  The c_k are multiplied in int32
+// groups (bound below 2^31 each); the running product of the groups is kept
+// as signed radix-2^31 digits r_0..r_{K-1} (r_i in [0, 2^31) below the top,
+// the top digit signed), so every digit is an int32 and digit * group is one
+// signed 32x32->64 multiply(-add).  A term enters 64-bit accumulators, one
+// per digit, in one of two ways:
+//   tail form:  the last group T (bound below 2^tb) is not folded into the
+//               digits; acc_i += r_i * T is one multiply-add per digit.  An
+//               item of 2^m terms fits when m <= 32 - tb.
+//   digit form: every group is folded in; acc_i +/-= r_i is a 64-bit add per
+//               digit.  An item fits when m <= 31.
+// No absolute values, sign masks or carry chains per term.  The item sum
+// sum_i acc_i 2^{31 i} is reduced modulo the primes once, at the end of the
+// item (Sec. 2.2: residues modulo co-primes).
+constexpr int kMaxGroups = 12;
+
+struct DigitPlan {
+  int tail_form;              // 1: tail form, 0: digit form
+  int tree;                   // group products as balanced trees (else chains)
+  int ng;                     // groups folded into the digits
+  int fac[kMaxN];             // factor indices (0-based k-1), group by group
+  int start[kMaxGroups + 1];  // group g: fac[start[g] .. start[g+1])
+  int ntail;                  // tail: fac[start[ng] .. start[ng] + ntail)
+  int tail_bits;              // tail bound < 2^tail_bits
+  int digits[kMaxGroups];     // digits of the product of groups 0..g
+  int kd;                     // digits of the folded product
+  int cost;                   // estimated multiply-pipe cycles per term
+  int max_m;                  // largest walk width of an item
 };
-__host__ __device__ constexpr BoundInfo make_bounds(int DELTA, int N) {
-  BoundInfo bi{};
-  GroupInfo gi = make_groups(DELTA, N);
+
+__host__ __device__ constexpr long long factor_bound(int DELTA, int N, int k) {
+  const long long L = 2LL * N - k - DELTA;
+  return L < 1 ? 1 : L;
+}
+
+// Groups of the factors idx[0..n) with bound < 2^31 each: contiguous greedy
+// in index order, or first-fit decreasing by bound into as few groups as it
+// finds.  Writes fac / start / ng.
+__host__ __device__ constexpr bool pack_groups(int DELTA, int N, const int* idx, int n,
+                                               bool greedy, DigitPlan& dp) {
+  if (greedy) {
+    int ng = 0, pos = 0;
+    long long pr = 1;
+    for (int i = 0; i < n; ++i) {
+      const long long L = factor_bound(DELTA, N, idx[i] + 1);
+      if (i == 0 || pr * L >= 2147483648LL) {
+        if (ng >= kMaxGroups) return false;
+        dp.start[ng++] = pos;
+        pr = 1;
+      }
+      pr *= L;
+      dp.fac[pos++] = idx[i];
+    }
+    dp.ng = ng;
+    dp.start[ng] = pos;
+    return true;
+  }
+  int ord[kMaxN] = {};
+  for (int i = 0; i < n; ++i) ord[i] = idx[i];
+  for (int i = 1; i < n; ++i) {          // largest bound first
+    const int v = ord[i];
+    int j = i - 1;
+    while (j >= 0 && factor_bound(DELTA, N, ord[j] + 1) < factor_bound(DELTA, N, v + 1)) {
+      ord[j + 1] = ord[j];
+      --j;
+    }
+    ord[j + 1] = v;
+  }
+  for (int nb = 1; nb <= kMaxGroups && nb <= n; ++nb) {
+    long long prod[kMaxGroups] = {};
+    int cnt[kMaxGroups] = {};
+    int member[kMaxGroups][kMaxN] = {};
+    for (int g = 0; g < nb; ++g) prod[g] = 1;
+    bool ok = true;
+    for (int i = 0; i < n && ok; ++i) {
+      const long long L = factor_bound(DELTA, N, ord[i] + 1);
+      int best = -1;                      // the fullest group that still fits
+      for (int g = 0; g < nb; ++g)
+        if (prod[g] * L < 2147483648LL && (best < 0 || prod[g] > prod[best])) best = g;
+      if (best < 0) {
+        ok = false;
+      } else {
+        prod[best] *= L;
+        member[best][cnt[best]++] = ord[i];
+      }
+    }
+    if (!ok) continue;
+    int pos = 0, ng = 0;
+    for (int g = 0; g < nb; ++g) {
+      if (!cnt[g]) continue;
+      dp.start[ng++] = pos;
+      for (int i = 0; i < cnt[g]; ++i) dp.fac[pos++] = member[g][i];
+    }
+    dp.ng = ng;
+    dp.start[ng] = pos;
+    return true;
+  }
+  return false;
+}
+
+// Digits after each folded group (from the exact bound, 8 x 32-bit limbs)
+// and the estimated cost: 2 multiply-pipe cycles per int32 product, 4 per
+// 32x32->64 product.
+__host__ __device__ constexpr void digit_counts(int DELTA, int N, DigitPlan& dp) {
   unsigned w[8] = {1, 0, 0, 0, 0, 0, 0, 0};
-  for (int g = 0; g < gi.g; ++g) {
-    for (int k = gi.start[g] + 1; k <= gi.start[g + 1]; ++k) {
-      long long L = 2LL * N - k - DELTA;
-      if (L < 1) L = 1;
+  int wide = 0;
+  dp.kd = 1;
+  for (int g = 0; g < dp.ng; ++g) {
+    for (int i = dp.start[g]; i < dp.start[g + 1]; ++i) {
+      const unsigned long long L = (unsigned long long)factor_bound(DELTA, N, dp.fac[i] + 1);
       unsigned long long carry = 0;
-      for (int i = 0; i < 8; ++i) {
-        unsigned long long t = (unsigned long long)w[i] * (unsigned long long)L + carry;
-        w[i] = (unsigned)t;
-        carry = t >> 32;
+      for (int j = 0; j < 8; ++j) {
+        const unsigned long long x = (unsigned long long)w[j] * L + carry;
+        w[j] = (unsigned)x;
+        carry = x >> 32;
       }
     }
     int top = 7;
     while (top > 0 && w[top] == 0) --top;
+    int bits = 0;
+    while (bits < 32 && (w[top] >> bits)) ++bits;
+    bits += top * 32;
+    const int k = (bits + 30) / 31;
+    if (g > 0) wide += dp.digits[g - 1];
+    dp.digits[g] = k < 1 ? 1 : k;
+    dp.kd = dp.digits[g];
+  }
+  if (dp.tail_form) wide += dp.kd;
+  const int nf = dp.start[dp.ng] + dp.ntail;
+  const int imul = nf - dp.ng - (dp.tail_form ? 1 : 0);
+  dp.cost = 2 * imul + 4 * wide + (dp.tail_form ? 0 : 1);
+}
+
+// Reorders the groups and the factors inside each group (a seeded shuffle;
+// the grouping itself is unchanged).  Different orders give the compiler
+// different instruction schedules of the same work.
+__host__ __device__ constexpr DigitPlan permute_plan(int DELTA, int N, DigitPlan dp,
+                                                     unsigned seed) {
+  if (!seed) return dp;
+  unsigned x = seed * 2654435761u + 12345u;
+  int order[kMaxGroups] = {};
+  for (int g = 0; g < dp.ng; ++g) order[g] = g;
+  for (int g = dp.ng - 1; g > 0; --g) {
+    x = x * 1664525u + 1013904223u;
+    const int j = (int)((x >> 8) % (unsigned)(g + 1));
+    const int t = order[g];
+    order[g] = order[j];
+    order[j] = t;
+  }
+  DigitPlan q = dp;
+  int pos = 0;
+  for (int g = 0; g < dp.ng; ++g) {
+    const int og = order[g], n = dp.start[og + 1] - dp.start[og];
+    int f[kMaxN] = {};
+    for (int i = 0; i < n; ++i) f[i] = dp.fac[dp.start[og] + i];
+    for (int i = n - 1; i > 0; --i) {
+      x = x * 1664525u + 1013904223u;
+      const int j = (int)((x >> 8) % (unsigned)(i + 1));
+      const int t = f[i];
+      f[i] = f[j];
+      f[j] = t;
+    }
+    q.start[g] = pos;
+    for (int i = 0; i < n; ++i) q.fac[pos++] = f[i];
+  }
+  q.start[dp.ng] = pos;
+  for (int i = 0; i < dp.ntail; ++i) q.fac[pos + i] = dp.fac[dp.start[dp.ng] + i];
+  digit_counts(DELTA, N, q);
+  if (q.ng == 0) q.kd = 1;
+  return q;
+}
+
+// How a (delta, n) kernel is planned: rule 0 picks the form, the tail and the
+// grouping of least estimated cost; rule 1 takes the tail form with the last
+// factors below 2^14 as tail and contiguous greedy groups.  The entries were
+// chosen by timing every variant on the GB300 (2^34-term slices of S(n),
+// L(n)); plans of equal cost can differ by 10-30 % in speed because the
+// compiler schedules them differently.
+struct PlanVariant {
+  int rule, greedy, tree;
+  unsigned seed;
+};
+__host__ __device__ constexpr PlanVariant plan_variant(int DELTA, int N) {
+  if (N < 14) return {0, 1, 0, 0};
+  if (N > 24) return {0, 0, 0, 0};
+  constexpr PlanVariant skolem[11] = {
+      {0, 1, 0, 0}, {0, 0, 0, 0}, {0, 1, 0, 0}, {0, 1, 1, 0}, {0, 1, 1, 0}, {1, 0, 1, 4},
+      {0, 0, 1, 2}, {1, 0, 1, 0}, {1, 0, 1, 0}, {0, 0, 1, 0}, {0, 1, 1, 0}};
+  constexpr PlanVariant langford[11] = {
+      {1, 0, 0, 0}, {0, 1, 1, 0}, {1, 0, 0, 0}, {0, 1, 1, 0}, {0, 0, 1, 0}, {0, 0, 1, 1},
+      {0, 0, 1, 1}, {0, 0, 1, 0}, {0, 1, 1, 0}, {0, 0, 0, 0}, {0, 1, 0, 0}};
+  return DELTA ? langford[N - 14] : skolem[N - 14];
+}
+
+// Smallest walk width the planner gives an item: long enough that its setup
+// and final reduction stay a small part of it.
+__host__ __device__ constexpr int digit_min_walk_bits(int N) {
+  return (2 * N - 1) < 12 ? (2 * N - 1) : 12;
+}
+
+__host__ __device__ constexpr DigitPlan make_digit_plan(int DELTA, int N) {
+  const PlanVariant pv = plan_variant(DELTA, N);
+  const int min_m = digit_min_walk_bits(N);
+  int all[kMaxN] = {};
+  for (int i = 0; i < N; ++i) all[i] = i;
+  DigitPlan best{};
+  best.cost = 1 << 30;
+  if (pv.rule == 1) {
+    long long tp = factor_bound(DELTA, N, N);
+    int t = N - 1;
+    while (t > 0 && tp * factor_bound(DELTA, N, t) < (1LL << 14)) {
+      tp *= factor_bound(DELTA, N, t);
+      --t;
+    }
     int b = 0;
-    while (b < 32 && (w[top] >> b)) ++b;
-    bi.bits[g] = top * 32 + b;
+    while ((1LL << b) <= tp) ++b;
+    DigitPlan dp{};
+    dp.tail_form = 1;
+    dp.ntail = N - t;
+    dp.tail_bits = b;
+    if (32 - b >= min_m && pack_groups(DELTA, N, all, t, true, dp)) {
+      for (int i = 0; i < dp.ntail; ++i) dp.fac[dp.start[dp.ng] + i] = t + i;
+      digit_counts(DELTA, N, dp);
+      dp.max_m = 32 - b;
+      best = dp;
+    }
   }
-  return bi;
+  if (best.cost == (1 << 30)) {
+    {
+      DigitPlan dp{};
+      if (pack_groups(DELTA, N, all, N, pv.greedy != 0, dp)) {
+        digit_counts(DELTA, N, dp);
+        dp.max_m = 31;
+        best = dp;
+      }
+    }
+    for (int tb = 4; tb <= 28; ++tb) {
+      // tail: the last factors (smallest bounds) while the bound stays < 2^tb
+      long long tp = factor_bound(DELTA, N, N);
+      if (tp >= (1LL << tb)) continue;
+      int t = N - 1;
+      while (t > 0 && tp * factor_bound(DELTA, N, t) < (1LL << tb)) {
+        tp *= factor_bound(DELTA, N, t);
+        --t;
+      }
+      int b = 0;
+      while ((1LL << b) <= tp) ++b;
+      if (32 - b < min_m) continue;
+      DigitPlan dp{};
+      dp.tail_form = 1;
+      dp.ntail = N - t;
+      dp.tail_bits = b;
+      if (t == 0) {
+        dp.ng = 0;
+        dp.start[0] = 0;
+      } else if (!pack_groups(DELTA, N, all, t, pv.greedy != 0, dp)) {
+        continue;
+      }
+      for (int i = 0; i < dp.ntail; ++i) dp.fac[dp.start[dp.ng] + i] = t + i;
+      digit_counts(DELTA, N, dp);
+      if (dp.ng == 0) dp.kd = 1;
+      dp.max_m = 32 - b;
+      if (dp.cost < best.cost || (dp.cost == best.cost && dp.max_m > best.max_m)) best = dp;
+    }
+  }
+  const int mm = best.max_m;
+  best = permute_plan(DELTA, N, best, pv.seed);
+  best.max_m = mm;
+  best.tree = pv.tree;
+  return best;
 }
-__host__ __device__ constexpr int limbs_of(int bits) { return bits < 1 ? 1 : (bits + 31) / 32; }
-// Headroom of the accumulator for the sum of 2^m terms of one item.
-constexpr int kLimbHeadroom = 26;
-__host__ __device__ constexpr int acc_limbs(int DELTA, int N) {
-  return limbs_of(make_bounds(DELTA, N).bits[make_groups(DELTA, N).g - 1] + 1 + kLimbHeadroom);
-}
-// Largest walk width m whose item sum fits the accumulator.
+
+// Largest walk width of an item whose sum fits the 64-bit digit accumulators.
 __host__ __device__ constexpr int limb_max_walk_bits(int DELTA, int N) {
-  return 32 * acc_limbs(DELTA, N) - make_bounds(DELTA, N).bits[make_groups(DELTA, N).g - 1] - 1;
+  return make_digit_plan(DELTA, N).max_m;
 }
 
-// acc += x (AL limbs, x already sign-extended), one carry chain.
-template <int AL>
-__device__ __forceinline__ void limbs_add(unsigned (&a)[AL], const unsigned (&x)[AL]) {
-  if constexpr (AL == 1) {
-    a[0] += x[0];
-  } else if constexpr (AL == 2) {
-    asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, %3;"
-        : "+r"(a[0]), "+r"(a[1]) : "r"(x[0]), "r"(x[1]));
-  } else if constexpr (AL == 3) {
-    asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, %4;\n\taddc.u32 %2, %2, %5;"
-        : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]) : "r"(x[0]), "r"(x[1]), "r"(x[2]));
-  } else if constexpr (AL == 4) {
-    asm("add.cc.u32 %0, %0, %4;\n\taddc.cc.u32 %1, %1, %5;\n\taddc.cc.u32 %2, %2, %6;\n\t"
-        "addc.u32 %3, %3, %7;"
-        : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3])
-        : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]));
-  } else if constexpr (AL == 5) {
-    asm("add.cc.u32 %0, %0, %5;\n\taddc.cc.u32 %1, %1, %6;\n\taddc.cc.u32 %2, %2, %7;\n\t"
-        "addc.cc.u32 %3, %3, %8;\n\taddc.u32 %4, %4, %9;"
-        : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4])
-        : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]));
-  } else if constexpr (AL == 6) {
-    asm("add.cc.u32 %0, %0, %6;\n\taddc.cc.u32 %1, %1, %7;\n\taddc.cc.u32 %2, %2, %8;\n\t"
-        "addc.cc.u32 %3, %3, %9;\n\taddc.cc.u32 %4, %4, %10;\n\taddc.u32 %5, %5, %11;"
-        : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5])
-        : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]));
+// Signed 32 x 32 -> 64 multiply(-add): one instruction on the device.
+__host__ __device__ __forceinline__ long long wide_mul_s32(int a, int b) {
+#ifdef __CUDA_ARCH__
+  long long d;
+  asm("mul.wide.s32 %0, %1, %2;" : "=l"(d) : "r"(a), "r"(b));
+  return d;
+#else
+  return (long long)a * b;
+#endif
+}
+__host__ __device__ __forceinline__ long long wide_mad_s32(int a, int b, long long c) {
+#ifdef __CUDA_ARCH__
+  long long d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+#else
+  return (long long)a * b + c;
+#endif
+}
+
+// Product of the n factors c[f[0..n)]: a balanced tree or a chain of int32
+// products (n and f are compile-time constants once the callers unroll).
+template <int NN>
+__host__ __device__ __forceinline__ int group_product(const int (&c)[NN], const int* f, int n,
+                                                      bool tree) {
+  if (tree) {
+    int v[NN];
+#pragma unroll
+    for (int i = 0; i < NN; ++i)
+      if (i < n) v[i] = c[f[i]];
+#pragma unroll
+    for (int w = 1; w < NN; w *= 2)
+#pragma unroll
+      for (int i = 0; i + w < NN; i += 2 * w)
+        if (i + w < n) v[i] *= v[i + w];
+    return v[0];
+  }
+  int v = c[f[0]];
+#pragma unroll
+  for (int i = 1; i < NN; ++i)
+    if (i < n) v *= c[f[i]];
+  return v;
+}
+
+// Digits r of one term's folded groups and its tail product T (tail form;
+// T = 1 in the digit form), negated when NEG:
+//   tail form:  (-1)^NEG prod_k c_k = T * sum_i r_i 2^{31 i}
+//   digit form: (-1)^NEG prod_k c_k = sum_i r_i 2^{31 i}
+template <int DELTA, int N, int NEG>
+__host__ __device__ __forceinline__ void digit_product(const int (&c)[N],
+                                                      int (&r)[make_digit_plan(DELTA, N).kd],
+                                                      int& T) {
+  constexpr DigitPlan dp = make_digit_plan(DELTA, N);
+  constexpr int K = dp.kd;
+  T = 1;
+  if constexpr (dp.tail_form) {
+    T = group_product(c, dp.fac + dp.start[dp.ng], dp.ntail, dp.tree != 0);
+    if constexpr (NEG) T = -T;
+  }
+  if constexpr (dp.ng == 0) {
+    r[0] = 1;
   } else {
-    static_assert(AL >= 1 && AL <= 6, "accumulator width");
-  }
-}
-
-// Accumulator of the exact form: the product of the |group products| as an
-// exact unsigned multi-limb integer (only as many limbs as the bounds need),
-// added with its sign into an exact two's-complement accumulator: a negative
-// term adds ~|t| and counts one in `ones` (-|t| = ~|t| + 1).  The item sum is
-// reduced modulo each prime once, at the end of the item.
-template <int DELTA, int N>
-struct LimbAcc {
-  static constexpr int NG = make_groups(DELTA, N).g;
-  static constexpr int PL = limbs_of(make_bounds(DELTA, N).bits[NG - 1]);
-  static constexpr int AL = acc_limbs(DELTA, N);
-  const Primes& P;
-  unsigned acc[AL];
-  int ones;
-  __device__ __forceinline__ explicit LimbAcc(const Primes& P_) : P(P_), ones(0) {
+    int G[dp.ng];
 #pragma unroll
-    for (int i = 0; i < AL; ++i) acc[i] = 0u;
-  }
-  template <int S>
-  __device__ __forceinline__ void term(const int (&c)[N]) {
-    constexpr GroupInfo gi = make_groups(DELTA, N);
-    constexpr BoundInfo bi = make_bounds(DELTA, N);
-    int G[gi.g];
-    group_products<DELTA, N>(c, G);
-    // sign of the term: parity of the negative groups, flipped on odd steps
-    unsigned sg = (S & 1) ? 0x80000000u : 0u;
+    for (int g = 0; g < dp.ng; ++g)
+      G[g] = group_product(c, dp.fac + dp.start[g], dp.start[g + 1] - dp.start[g], dp.tree != 0);
+    if constexpr (!dp.tail_form && NEG) G[0] = -G[0];
+    r[0] = G[0];
 #pragma unroll
-    for (int g = 0; g < gi.g; ++g) sg ^= (unsigned)G[g];
-    const unsigned m = (unsigned)((int)sg >> 31);
-    unsigned a[gi.g];
+    for (int g = 1; g < dp.ng; ++g) {
+      const int kc = dp.digits[g - 1], kn = dp.digits[g];
+      long long carry = 0;
 #pragma unroll
-    for (int g = 0; g < gi.g; ++g) a[g] = (unsigned)abs(G[g]);
-    unsigned p[PL];
-    if constexpr (gi.g == 1) {
-      p[0] = a[0];
-    } else {
-      constexpr int L1 = limbs_of(bi.bits[1]);
-      const unsigned long long t = (unsigned long long)a[0] * a[1];
-      p[0] = (unsigned)t;
-      if constexpr (L1 > 1) p[1] = (unsigned)(t >> 32);
-#pragma unroll
-      for (int g = 2; g < gi.g; ++g) {
-        const int lp = limbs_of(bi.bits[g - 1]);      // limbs so far
-        const int ln = limbs_of(bi.bits[g]);          // limbs after this factor
-        unsigned carry = 0;
-#pragma unroll
-        for (int i = 0; i < ln; ++i) {
-          if (i < lp) {
-            if (i == ln - 1) {
-              p[i] = p[i] * a[g] + carry;               // top limb: no carry out
-            } else {
-              const unsigned long long t2 = (unsigned long long)p[i] * a[g] + carry;
-              p[i] = (unsigned)t2;
-              carry = (unsigned)(t2 >> 32);
-            }
+      for (int i = 0; i < K; ++i) {
+        if (i < kn) {
+          const long long v = (i < kc) ? (i == 0 ? wide_mul_s32(r[i], G[g])
+                                                 : wide_mad_s32(r[i], G[g], carry))
+                                       : carry;
+          if (i < kn - 1) {
+            r[i] = (int)((unsigned)v & 0x7FFFFFFFu);
+            carry = v >> 31;
           } else {
-            p[i] = carry;                                // the new top limb
+            r[i] = (int)v;
           }
         }
       }
     }
-    unsigned x[AL];
+  }
+}
+
+// Reductions for a modulus p in (2^62 - 2^31, 2^62), the window every prime
+// of the exact count lies in.
+// a mod p in [0, p) for any signed 64-bit a: a quotient estimate in double
+// precision is off by at most one, which one correction on each side fixes.
+__host__ __device__ __forceinline__ unsigned long long signed_mod(long long a,
+                                                                 unsigned long long p) {
+  const long long q = (long long)((double)a / (double)p);
+  long long r = a - q * (long long)p;        // |r| < 2p: no overflow
+  if (r < 0) r += (long long)p;
+  if (r >= (long long)p) r -= (long long)p;
+  if (r < 0) r += (long long)p;
+  return (unsigned long long)r;
+}
+// (u 2^31 + a) mod p for u, a in [0, p): with u = uh 2^31 + ul and
+// 2^62 = p + delta (0 < delta < 2^31), u 2^31 == uh delta + ul 2^31.
+__host__ __device__ __forceinline__ unsigned long long horner31_mod(unsigned long long u,
+                                                                   unsigned long long a,
+                                                                   unsigned long long p) {
+  const unsigned long long delta = (1ULL << 62) - p;
+  unsigned long long v = (u >> 31) * delta + ((u & 0x7FFFFFFFULL) << 31) + a;   // < 3 * 2^62
+  v = (v >> 62) * delta + (v & ((1ULL << 62) - 1));                            // < 2^62 + 2^33
+  if (v >= p) v -= p;
+  if (v >= p) v -= p;
+  return v;
+}
+
+// Accumulator of the exact form: one 64-bit signed word per digit.
+template <int DELTA, int N>
+struct LimbAcc {
+  static constexpr int K = make_digit_plan(DELTA, N).kd;
+  static constexpr int TAIL = make_digit_plan(DELTA, N).tail_form;
+  const Primes& P;
+  long long acc[K];
+  __device__ __forceinline__ explicit LimbAcc(const Primes& P_) : P(P_) {
 #pragma unroll
-    for (int i = 0; i < AL; ++i) x[i] = (i < PL) ? (p[i] ^ m) : m;
-    limbs_add<AL>(acc, x);
-    ones -= (int)m;
+    for (int i = 0; i < K; ++i) acc[i] = 0;
+  }
+  template <int S>
+  __device__ __forceinline__ void term(const int (&c)[N]) {
+    int r[K];
+    int T;
+    digit_product<DELTA, N, (S & 1)>(c, r, T);
+    if constexpr (TAIL) {
+#pragma unroll
+      for (int i = 0; i < K; ++i) acc[i] = wide_mad_s32(r[i], T, acc[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < K; ++i) acc[i] += (long long)r[i];
+    }
   }
   __device__ __forceinline__ void negate() {
 #pragma unroll
-    for (int i = 0; i < AL; ++i) acc[i] = ~acc[i];   // -(acc + ones) = ~acc + (1 - ones)
-    ones = 1 - ones;
+    for (int i = 0; i < K; ++i) acc[i] = -acc[i];
   }
+  // residues of (flip ? -1 : 1) * sum_i acc_i 2^{31 i}, in [0, p)
   __device__ __forceinline__ void finish(bool flip, int nprimes,
                                          unsigned long long (&res)[kMaxPrimes]) {
-    if (flip) negate();
-    unsigned x[AL];
-    const unsigned sx = (unsigned)(ones >> 31);
 #pragma unroll
-    for (int i = 0; i < AL; ++i) x[i] = (i == 0) ? (unsigned)ones : sx;
-    limbs_add<AL>(acc, x);
+    for (int j = 0; j < kMaxPrimes; ++j) {
+      if (j >= nprimes) {
+        res[j] = 0;
+        continue;
+      }
+      const unsigned long long p = (unsigned long long)P.pr[j].p;
+      unsigned long long u = 0;
 #pragma unroll
-    for (int i = 0; i < kMaxPrimes; ++i) {
-      if (i >= nprimes) { res[i] = 0; continue; }
-      const long long p = P.pr[i].p;
-      long long r = (long long)(int)acc[AL - 1] % p;
-      if (r < 0) r += p;
-      unsigned long long u = (unsigned long long)r;
-#pragma unroll
-      for (int j = AL - 2; j >= 0; --j)
-        u = (unsigned long long)((((unsigned __int128)u << 32) | acc[j]) % (unsigned long long)p);
-      res[i] = u;
+      for (int i = K - 1; i >= 0; --i) u = horner31_mod(u, signed_mod(acc[i], p), p);
+      res[j] = (flip && u) ? p - u : u;
     }
   }
 };
@@ -512,7 +802,7 @@ __device__ __forceinline__ void run_item(unsigned long long pres, int m, unsigne
     c[k - 1] = __popcll(pm) - 2 * __popcll(pm & (neg ^ (neg >> d)));
   }
   // w = 2x (0 off the span); inner positions start at +1
-  signed char* ws = ws_col + PAD * kWsStride;
+  const unsigned wsa = (unsigned)__cvta_generic_to_shared(ws_col) + PAD * kWsStride;
   for (int i = -PAD; i < 2 * N + 1 + PAD; ++i) {
     int v = 0;
     if (i >= 0 && i < 64) {
@@ -520,11 +810,11 @@ __device__ __forceinline__ void run_item(unsigned long long pres, int m, unsigne
       const int negative = (int)((neg >> i) & 1ULL);
       v = present ? (negative ? -2 : 2) : 0;
     }
-    ws[i * kWsStride] = (signed char)v;
+    sts_s8(wsa + (unsigned)(i * kWsStride), v);
   }
   int near[NEAR];
 #pragma unroll
-  for (int i = 0; i < NEAR; ++i) near[i] = (int)ws[(U + i) * kWsStride];
+  for (int i = 0; i < NEAR; ++i) near[i] = lds_s8(wsa + (unsigned)((U + i) * kWsStride));
   // sign of prod x at the first block; every outer flip negates it, which the
   // loop applies by negating the accumulator (see below)
   const int sb0 = (__popcll(neg) & 1) ? -1 : 1;
@@ -534,7 +824,7 @@ __device__ __forceinline__ void run_item(unsigned long long pres, int m, unsigne
     if (b + 1 == nblocks) break;
     inner_update<DELTA, N, U, 0>(c, near);             // inner bits back to +1
     const int J = U + __ffsll((long long)(b + 1)) - 1;
-    outer_flip<DELTA, N, U>(J, c, near, ws);
+    outer_flip<DELTA, N, U>(J, c, near, wsa);
     // block b+1 has the opposite sign of prod x: negate what was summed so far
     // and keep adding with the same signs; the total is fixed once below
     A.negate();

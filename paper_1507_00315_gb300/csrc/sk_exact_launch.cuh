@@ -9,8 +9,8 @@
 // bit-exact whatever the schedule).
 //
 // Two arithmetic forms of the term product (same residues):
-//   limb_kernel<delta, n>       -- exact multi-limb products and sums, reduced
-//                                  modulo the primes once per work item;
+//   limb_kernel<delta, n>       -- exact signed-digit products and sums,
+//                                  reduced modulo the primes once per item;
 //   mont_kernel<delta, n, NPR>  -- per-term signed Montgomery products modulo
 //                                  each 62-bit prime.
 #pragma once
@@ -78,7 +78,7 @@ __device__ __forceinline__ void warp_flush(unsigned long long (&tot)[kMaxPrimes]
   }
 }
 
-// One exact-limb work item, compiled once per (delta, n) and called by both
+// One exact-form work item, compiled once per (delta, n) and called by both
 // the single-job kernel and the batch kernel.
 template <int DELTA, int N>
 __device__ __noinline__ Res4 limb_item(unsigned long long pres, int m, unsigned long long item,
@@ -217,7 +217,7 @@ typedef cudaError_t (*ExactLaunchFn)(const ExactLaunch&);
 
 // Montgomery-form launchers for delta in {0, 1}, n in [1, kMaxN], three
 // primes (null for combinations that were not compiled; four moduli go
-// through the exact-limb form).
+// through the exact form).
 ExactLaunchFn exact_launcher(int delta, int n, int nprimes);
 // Exact-limb launchers for delta in {0, 1}, n in [1, kMaxN].
 ExactLaunchFn limb_launcher(int delta, int n);

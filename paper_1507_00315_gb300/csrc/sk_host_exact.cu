@@ -69,7 +69,7 @@ ExactLaunchFn limb_launcher(int delta, int n) {
   return kLimbTable[n][delta];
 }
 
-// Largest walk width of the exact-limb form (compile-time table per (delta, n)).
+// Largest walk width of the exact form (compile-time table per (delta, n)).
 template <int D, int N>
 struct LimbMaxM { static constexpr int v = limb_max_walk_bits(D, N); };
 #define SK_LM(N) {LimbMaxM<0, N>::v, LimbMaxM<1, N>::v}
@@ -143,7 +143,7 @@ static int make_plan(int variant, int n, const sk_count_opts* o, Plan* pl) {
 }
 
 // Multiplies raw residues of the Montgomery form by R^{e}, e = groups - 2,
-// removing the factor every term carries (the limb form has none).
+// removing the factor every term carries (the exact form has none).
 static void unmont(const Plan& pl, uint64_t* res) {
   if (pl.arith != SK_ARITH_MONTGOMERY) return;
   GroupInfo gi = make_groups(pl.delta, pl.n);

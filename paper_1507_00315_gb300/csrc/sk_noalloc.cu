@@ -5,7 +5,7 @@
 // cudaMalloc can fail or fragment it under memory pressure), and
 // latency-sensitive host loops that cannot absorb the device-wide
 // synchronisation cudaFree implies.  This entry point runs the same
-// Gray-code kernel as skolem_item_residues (exact-limb form), but its device
+// Gray-code kernel as skolem_item_residues (exact form), but its device
 // scratch -- the
 // launch record (work counter, residue slots, error word) and the per-item
 // staging of the residues before they are copied to the caller's host
