@@ -1,64 +1,54 @@
 // sk_gemm_tc.cuh -- BF16 GEMM on the 5th-generation tensor cores (tcgen05)
-// for the proposal network's forward pass: C[M x N] = A[M x K] * B^T, A stored
-// row-major [M][K] (activations), B stored [N][K] (the weights kept K-major),
-// FP32 accumulation in tensor memory, fused bias + ReLU -> bf16 or fp32 out.
+// for the proposal network's forward pass: C[M x N] = A[M x K] * B^T + bias,
+// A row-major [M][K] (activations), B stored [N][K] (the weights kept
+// K-major), FP32 accumulation in tensor memory, fused bias (+ ReLU -> bf16)
+// epilogue.  M % 128 == 0, N % 256 == 0, K % 64 == 0, K <= 256.
 //
-// One CTA (4 warps) per 128 x 256 output tile.  Each 64-wide K slice of A
-// (128 x 64) and B (256 x 64) is copied by cp.async into shared memory in the
-// canonical no-swizzle K-major layout -- 8-row x 16-byte core matrices, the 8
-// core matrices of one 8-row group along K contiguous (128 B apart), groups
-// 1024 B apart -- two stages deep.  One thread issues four tcgen05.mma
-// (K = 16 each) per slice into a 128-lane x 256-column fp32 accumulator in
-// tensor memory and commits them to an mbarrier; the slice's buffer is
-// refilled only after that mbarrier flips.  Every wait is bounded: on expiry
-// the kernel records an error word, waits (bounded) for its own MMAs,
-// releases its tensor memory and returns.  The epilogue reads the accumulator
-// with tcgen05.ld (each warp its 32 lanes = rows).
+// Persistent and warp-specialised, one CTA (6 warps) per SM:
+//   * every CTA owns one 256-wide column tile of B for the whole launch: its
+//     K/64 slices ([256][64] bf16, 128-byte swizzle) are loaded once by TMA
+//     and stay in shared memory;
+//   * warp 0 (one lane) streams the CTA's 128-row tiles of A by TMA, one
+//     [128][64] slice per stage of a 4-deep ring (mbarriers full / empty);
+//   * warp 1 (one lane) issues tcgen05.mma (128 x 256 x 16) for each slice
+//     into one of two 256-column accumulators in tensor memory and commits
+//     them to the ring's "empty" barrier and, per tile, to "acc full";
+//   * warps 2-5 (the epilogue) read the finished accumulator with
+//     tcgen05.ld (each warp its 32 lanes = rows), add the bias, apply ReLU
+//     and round to bf16 (or keep fp32), write each 128-byte column slab of
+//     their 32 rows into a 128-byte-swizzled staging buffer in shared memory
+//     (two per warp) and store it to global memory with one TMA bulk-tensor
+//     store, then release the accumulator ("acc empty") so the MMA warp can
+//     start the tile after next while the epilogue of this one runs.
+// Every wait is bounded (poll count and 2 s of %globaltimer): on expiry the
+// role records an error word and stops; before the CTA frees its tensor
+// memory each role waits (bounded) for its own copies and MMAs in flight.
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
+
 #include <cstdint>
 
 namespace sk {
 
-constexpr int kTcBM = 128, kTcBN = 256, kTcBK = 64, kTcStages = 2;
-constexpr int kTcTileA = kTcBM * kTcBK * 2;          // 16 KB
-constexpr int kTcTileB = kTcBN * kTcBK * 2;          // 32 KB
-constexpr int kTcSmem = kTcStages * (kTcTileA + kTcTileB) + 1024;
-constexpr unsigned kTcWaitLimit = 1u << 22;          // polls
-constexpr unsigned long long kTcWaitNs = 2000000000ULL;    // and at most 2 s
+constexpr int kTcBM = 128, kTcBN = 256, kTcBK = 64, kTcStages = 3, kTcMaxK = 256;
+constexpr int kTcSliceA = kTcBM * kTcBK * 2;                  // 16 KB
+constexpr int kTcSliceB = kTcBN * kTcBK * 2;                  // 32 KB
+constexpr int kTcStage = 32 * 128;                            // staging: 32 rows x 128 B
+constexpr int kTcThreads = 192;                               // 6 warps
+constexpr int kTcSmem =
+    (kTcMaxK / kTcBK) * kTcSliceB + kTcStages * kTcSliceA + 4 * 2 * kTcStage + 1024;
+constexpr unsigned kTcWaitLimit = 1u << 24;                   // polls
+constexpr unsigned long long kTcWaitNs = 2000000000ULL;       // and at most 2 s
 
 struct TcGemmArgs {
-  int M, N, K;                    // M % 128 == 0, N % 256 == 0, K % 64 == 0
-  const __nv_bfloat16* A;         // [M][lda]
-  int lda;
-  const __nv_bfloat16* Bt;        // [N][ldb]
-  int ldb;
-  void* C;                        // [M][ldc] bf16 (relu) or fp32
-  int ldc;
+  int M, N, K;
   const float* bias;              // [N] or null
-  int relu_bf16;                  // 1: bf16(relu(acc + bias)); 0: fp32 acc + bias
   unsigned* err;                  // set nonzero if a wait gave up
 };
 
 __device__ __forceinline__ unsigned tc_smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
-}
-
-// Shared-memory matrix descriptor, no swizzle: start address, leading
-// (K-direction) and stride (M/N-direction) byte offsets, version 1.
-__device__ __forceinline__ unsigned long long tc_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
-  unsigned long long d = 0;
-  d |= (unsigned long long)((saddr >> 4) & 0x3FFF);
-  d |= (unsigned long long)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (unsigned long long)((sbo >> 4) & 0x3FFF) << 32;
-  d |= 1ULL << 46;                                 // descriptor version
-  return d;                                        // layout type 0: no swizzle
-}
-
-// Instruction descriptor of kind::f16: D fp32, A and B bf16, both K-major.
-__host__ __device__ constexpr unsigned tc_idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) |
-         ((unsigned)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ unsigned long long tc_now() {
@@ -67,10 +57,10 @@ __device__ __forceinline__ unsigned long long tc_now() {
   return t;
 }
 
+// Bounded wait for the completion of the phase with the given parity.
 __device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity) {
   const unsigned long long t0 = tc_now();
   for (unsigned it = 0; it < kTcWaitLimit; ++it) {
-    if ((it & 255) == 255 && tc_now() - t0 > kTcWaitNs) return false;
     unsigned ok;
     asm volatile(
         "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
@@ -78,146 +68,267 @@ __device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity) {
         : "r"(mbar), "r"(parity)
         : "memory");
     if (ok) return true;
+    if ((it & 255) == 255 && tc_now() - t0 > kTcWaitNs) return false;
   }
   return false;
 }
 
-// Copies rows [r0, r0 + rows) x k-slice [k0, k0 + 64) of a row-major bf16
-// matrix into the canonical core-matrix layout at smem `dst`.
-__device__ __forceinline__ void tc_load_tile(unsigned char* dst, const __nv_bfloat16* src, int ld,
-                                             int r0, int k0, int rows) {
-  const int chunks = rows * (kTcBK / 8);          // 16-byte chunks
-  for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
-    const int r = c >> 3, kc = c & 7;
-    const unsigned off = (unsigned)(((r >> 3) * 8 + kc) * 128 + (r & 7) * 16);
-    const void* g = src + (size_t)(r0 + r) * ld + k0 + kc * 8;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tc_smem_u32(dst + off)),
-                 "l"(g));
-  }
+__device__ __forceinline__ void tc_expect_tx(unsigned mbar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
+               : "memory");
 }
 
-__global__ void __launch_bounds__(128, 1) gemm_tc_kernel(TcGemmArgs g) {
+__device__ __forceinline__ void tc_arrive(unsigned mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// 2D TMA load of the box at (x = column, y = row) into shared memory.
+__device__ __forceinline__ void tc_tma_load(unsigned dst, const CUtensorMap* map, int x, int y,
+                                            unsigned mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+
+// 2D TMA store of the staged box at (x = column, y = row); one bulk group.
+__device__ __forceinline__ void tc_tma_store(const CUtensorMap* map, unsigned src, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map),
+      "r"(x), "r"(y), "r"(src)
+      : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor, K-major, 128-byte swizzle: 8-row groups
+// of 128-byte rows 1024 bytes apart (stride byte offset), version 1.
+__device__ __forceinline__ unsigned long long tc_desc_sw128(unsigned saddr) {
+  unsigned long long d = 0;
+  d |= (unsigned long long)((saddr >> 4) & 0x3FFF);
+  d |= 1ULL << 16;                                   // leading byte offset (unused)
+  d |= (unsigned long long)(1024 >> 4) << 32;        // stride byte offset
+  d |= 1ULL << 46;                                   // descriptor version
+  d |= 2ULL << 61;                                   // layout: 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16: D fp32, A and B bf16, both K-major.
+__host__ __device__ constexpr unsigned tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) |
+         ((unsigned)(M >> 4) << 24);
+}
+
+// BF16 = 1: C = bf16(relu(acc + bias)); 0: C = fp32 (acc + bias).
+template <int BF16>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap amap,
+                   const __grid_constant__ CUtensorMap bmap,
+                   const __grid_constant__ CUtensorMap cmap, TcGemmArgs g) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
-  __shared__ __align__(8) unsigned long long mbar[kTcStages];
+  __shared__ __align__(8) unsigned long long full_bar[kTcStages], empty_bar[kTcStages];
+  __shared__ __align__(8) unsigned long long b_bar, accf_bar[2], acce_bar[2];
   __shared__ unsigned tmem_base_s;
+  __shared__ float sbias[kTcBN];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * kTcBN;
   unsigned char* base = (unsigned char*)(((size_t)tc_smem + 1023) & ~(size_t)1023);
-  unsigned char* sA[kTcStages];
-  unsigned char* sB[kTcStages];
-  for (int s = 0; s < kTcStages; ++s) {
-    sA[s] = base + s * (kTcTileA + kTcTileB);
-    sB[s] = sA[s] + kTcTileA;
+  const int nkb = g.K / kTcBK;                       // K slices per tile
+  unsigned char* sB = base;                          // nkb x [256][64]
+  unsigned char* sA = base + nkb * kTcSliceB;        // ring of [128][64]
+  unsigned char* sC = sA + kTcStages * kTcSliceA;    // 4 warps x 2 staging buffers
+  const int NT = g.N / kTcBN, MT = g.M / kTcBM;
+  const int groups = gridDim.x / NT;                 // CTAs per column tile
+  const int nt = blockIdx.x % NT, m_first = blockIdx.x / NT;
+  const int my_tiles = (m_first < MT) ? (MT - m_first + groups - 1) / groups : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&full_bar[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&empty_bar[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&b_bar)));
+    for (int a = 0; a < 2; ++a) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&accf_bar[a])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(tc_smem_u32(&acce_bar[a])));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      tc_smem_u32(&tmem_base_s)),
-                 "r"(256));
+                 "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kTcStages; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&mbar[s])));
-    asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const unsigned tmem = tmem_base_s;
-  const unsigned idesc = tc_idesc(kTcBM, kTcBN);
-  const int nk = g.K / kTcBK;
-  unsigned phase[kTcStages] = {0, 0};
-  bool pending[kTcStages] = {false, false};
-  bool ok = true;
 
-  // prologue: slice 0 into stage 0
-  tc_load_tile(sA[0], g.A, g.lda, m0, 0, kTcBM);
-  tc_load_tile(sB[0], g.Bt, g.ldb, n0, 0, kTcBN);
-  asm volatile("cp.async.commit_group;");
-  for (int kb = 0; kb < nk; ++kb) {
-    const int s = kb & 1;
-    // next slice into the other stage once its previous MMAs are done
-    if (kb + 1 < nk) {
-      const int s2 = s ^ 1;
-      if (pending[s2]) {
-        if (!tc_wait(tc_smem_u32(&mbar[s2]), phase[s2])) ok = false;
-        phase[s2] ^= 1;
-        pending[s2] = false;
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      bool ok = true;
+      const unsigned bb = tc_smem_u32(&b_bar);
+      tc_expect_tx(bb, (unsigned)(nkb * kTcSliceB));
+      for (int kb = 0; kb < nkb; ++kb)
+        tc_tma_load(tc_smem_u32(sB + kb * kTcSliceB), &bmap, kb * kTcBK, nt * kTcBN, bb);
+      unsigned u = 0;                                // slices issued
+      for (int t = 0; t < my_tiles && ok; ++t) {
+        const int mt = m_first + t * groups;
+        for (int kb = 0; kb < nkb && ok; ++kb, ++u) {
+          const int s = (int)(u % kTcStages);
+          const unsigned ph = (u / kTcStages) & 1u;
+          if (!tc_wait(tc_smem_u32(&empty_bar[s]), ph ^ 1u)) {
+            ok = false;
+            break;
+          }
+          const unsigned fb = tc_smem_u32(&full_bar[s]);
+          tc_expect_tx(fb, (unsigned)kTcSliceA);
+          tc_tma_load(tc_smem_u32(sA + s * kTcSliceA), &amap, kb * kTcBK, mt * kTcBM, fb);
+        }
       }
-      tc_load_tile(sA[s2], g.A, g.lda, m0, (kb + 1) * kTcBK, kTcBM);
-      tc_load_tile(sB[s2], g.Bt, g.ldb, n0, (kb + 1) * kTcBK, kTcBN);
-      asm volatile("cp.async.commit_group;");
-      asm volatile("cp.async.wait_group 1;");
-    } else {
-      asm volatile("cp.async.wait_group 0;");
+      if (!ok) atomicOr(g.err, 1u);
+      // wait for this thread's copies in flight: the last use of every stage
+      // and the resident slices of B
+      for (int s = 0; s < kTcStages; ++s) {
+        if ((unsigned)s >= u) break;
+        const unsigned last = u - 1 - ((u - 1 - (unsigned)s) % kTcStages);
+        if (!tc_wait(tc_smem_u32(&full_bar[s]), (last / kTcStages) & 1u)) atomicOr(g.err, 8u);
+      }
+      if (!tc_wait(bb, 0)) atomicOr(g.err, 8u);
     }
-    asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const unsigned a0 = tc_smem_u32(sA[s]), b0 = tc_smem_u32(sB[s]);
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      bool ok = tc_wait(tc_smem_u32(&b_bar), 0);
+      const unsigned idesc = tc_idesc(kTcBM, kTcBN);
+      unsigned u = 0;
+      int committed = -1;                            // last tile committed to acc full
+      for (int t = 0; t < my_tiles && ok; ++t) {
+        const int acc = t & 1;
+        if (!tc_wait(tc_smem_u32(&acce_bar[acc]), ((t >> 1) & 1) ^ 1)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const unsigned d = tmem + (unsigned)(acc * kTcBN);
+        for (int kb = 0; kb < nkb && ok; ++kb, ++u) {
+          const int s = (int)(u % kTcStages);
+          if (!tc_wait(tc_smem_u32(&full_bar[s]), (u / kTcStages) & 1u)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const unsigned a0 = tc_smem_u32(sA + s * kTcSliceA);
+          const unsigned b0 = tc_smem_u32(sB + kb * kTcSliceB);
 #pragma unroll
-      for (int kk = 0; kk < kTcBK / 16; ++kk) {
-        // a K = 16 step covers two core matrices along K (2 x 128 B)
-        const unsigned long long ad = tc_desc(a0 + kk * 256, 128, 1024);
-        const unsigned long long bd = tc_desc(b0 + kk * 256, 128, 1024);
-        const unsigned acc = (kb > 0 || kk > 0) ? 1u : 0u;
+          for (int kk = 0; kk < kTcBK / 16; ++kk) {
+            // K = 16 bf16 = 32 bytes further along the swizzled 128-byte rows
+            const unsigned long long ad = tc_desc_sw128(a0 + kk * 32);
+            const unsigned long long bd = tc_desc_sw128(b0 + kk * 32);
+            const unsigned accum = (kb > 0 || kk > 0) ? 1u : 0u;
+            asm volatile(
+                "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+          }
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  tc_smem_u32(&empty_bar[s])));
+        }
+        if (!ok) break;
         asm volatile(
-            "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                tc_smem_u32(&accf_bar[acc])));
+        committed = t;
       }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              tc_smem_u32(&mbar[s])));
+      if (!ok) atomicOr(g.err, 2u);
+      // wait for this thread's MMAs in flight (the last commit of each
+      // accumulator completes after every MMA issued before it)
+      for (int t = committed; t >= 0 && t > committed - 2; --t)
+        if (!tc_wait(tc_smem_u32(&accf_bar[t & 1]), (t >> 1) & 1)) atomicOr(g.err, 8u);
     }
-    pending[s] = true;
-    __syncthreads();
-  }
-  // wait for the last MMAs of both stages
-  for (int s = 0; s < kTcStages; ++s)
-    if (pending[s]) {
-      if (!tc_wait(tc_smem_u32(&mbar[s]), phase[s])) ok = false;
-      phase[s] ^= 1;
-    }
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (!ok) {
-    if (lane == 0) atomicOr(g.err, 1u);
   } else {
-    // epilogue: warp w reads lanes 32w..32w+31 (rows), 8 columns at a time
-    const int row = m0 + warp * 32 + lane;
-    for (int c0 = 0; c0 < kTcBN; c0 += 8) {
-      unsigned v[8];
-      const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-            "=r"(v[7])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      float f[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        f[i] = __uint_as_float(v[i]);
-        if (g.bias) f[i] += g.bias[n0 + c0 + i];
+    // ---------------------------------------------------------------- epilogue
+    const int q = warp & 3;                          // TMEM lane quarter of this warp
+    constexpr int kCols = BF16 ? 64 : 32;            // columns per 128-byte slab
+    unsigned char* stage0 = sC + q * 2 * kTcStage;
+    // the bias of this CTA's column tile, staged once (named barrier of the
+    // 128 epilogue threads)
+    for (int i = threadIdx.x - 64; i < kTcBN; i += 128)
+      sbias[i] = g.bias ? __ldg(g.bias + nt * kTcBN + i) : 0.f;
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    bool ok = true;
+    unsigned slab = 0;                               // slabs stored by this warp
+    for (int t = 0; t < my_tiles; ++t) {
+      const int acc = t & 1;
+      const int mt = m_first + t * groups;
+      if (!tc_wait(tc_smem_u32(&accf_bar[acc]), (t >> 1) & 1)) {
+        ok = false;
+        break;
       }
-      if (g.relu_bf16) {
-        __nv_bfloat162* dst =
-            (__nv_bfloat162*)((__nv_bfloat16*)g.C + (size_t)row * g.ldc + n0 + c0);
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int n0 = nt * kTcBN, row0 = mt * kTcBM + q * 32;
+#pragma unroll 1
+      for (int c0 = 0; c0 < kTcBN; c0 += kCols, ++slab) {
+        // the staging buffer of two slabs ago must have been read out
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        __syncwarp();
+        unsigned char* st = stage0 + (slab & 1) * kTcStage;
+        // all loads of the slab first, one wait
+        unsigned v[kCols];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-          dst[i] = __floats2bfloat162_rn(fmaxf(f[2 * i], 0.f), fmaxf(f[2 * i + 1], 0.f));
-      } else {
-        float4* dst = (float4*)((float*)g.C + (size_t)row * g.ldc + n0 + c0);
-        dst[0] = make_float4(f[0], f[1], f[2], f[3]);
-        dst[1] = make_float4(f[4], f[5], f[6], f[7]);
+        for (int h = 0; h < kCols / 16; ++h) {       // 16 accumulator columns per load
+          const unsigned taddr =
+              tmem + ((unsigned)(q * 32) << 16) + (unsigned)(acc * kTcBN + c0 + h * 16);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+              "%12,%13,%14,%15}, [%16];"
+              : "=r"(v[h * 16 + 0]), "=r"(v[h * 16 + 1]), "=r"(v[h * 16 + 2]), "=r"(v[h * 16 + 3]),
+                "=r"(v[h * 16 + 4]), "=r"(v[h * 16 + 5]), "=r"(v[h * 16 + 6]), "=r"(v[h * 16 + 7]),
+                "=r"(v[h * 16 + 8]), "=r"(v[h * 16 + 9]), "=r"(v[h * 16 + 10]),
+                "=r"(v[h * 16 + 11]), "=r"(v[h * 16 + 12]), "=r"(v[h * 16 + 13]),
+                "=r"(v[h * 16 + 14]), "=r"(v[h * 16 + 15])
+              : "r"(taddr));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        unsigned w[32];                              // this row's 128 bytes of the slab
+#pragma unroll
+        for (int i = 0; i < kCols; ++i) {
+          const float f = __uint_as_float(v[i]) + sbias[c0 + i];
+          if constexpr (BF16) {
+            const unsigned b16 = __bfloat16_as_ushort(__float2bfloat16_rn(fmaxf(f, 0.f)));
+            if (i & 1) w[i / 2] |= b16 << 16;
+            else       w[i / 2] = b16;
+          } else {
+            w[i] = __float_as_uint(f);
+          }
+        }
+        // row `lane` of the slab, 16-byte chunk c at chunk position c ^ (row & 7)
+        // (the layout a 128-byte-swizzled TMA store reads)
+        const unsigned rbase = tc_smem_u32(st) + (unsigned)lane * 128u;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const unsigned addr = rbase + (unsigned)((c ^ (lane & 7)) * 16);
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w[4 * c]),
+                       "r"(w[4 * c + 1]), "r"(w[4 * c + 2]), "r"(w[4 * c + 3])
+                       : "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) tc_tma_store(&cmap, tc_smem_u32(st), n0 + c0, row0);
       }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      tc_arrive(tc_smem_u32(&acce_bar[acc]));
     }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    if (!ok && lane == 0) atomicOr(g.err, 4u);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
 }
 
 }  // namespace sk

@@ -6,6 +6,7 @@
 // loss: cross entropy of the masked softmax.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -28,20 +29,35 @@ cudaError_t gemm(const GemmArgs& g, int splits, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// X[b][i] = occupancy of bin i of state b (0 beyond 2n).
-__global__ void mlp_inputs_kernel(const unsigned char* __restrict__ slots, int B, int n, int delta,
-                                  int K1, __nv_bfloat16* X) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+// X[b][i] = occupancy of bin i of state b (0 beyond 2n; n <= 40, so the
+// bins fit a 128-entry histogram).  One warp per
+// state: the pairs are counted into a shared histogram, then each lane
+// writes four adjacent bf16 inputs (one 8-byte store; a row is 256 bytes).
+__global__ void __launch_bounds__(256) mlp_inputs_kernel(const unsigned char* __restrict__ slots,
+                                                         int B, int n, int delta, int K1,
+                                                         __nv_bfloat16* X) {
+  __shared__ unsigned occ[8][128];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.x * 8 + w;
   if (b >= B) return;
-  unsigned char occ[2 * kPtMaxN];
-  for (int i = 0; i < 2 * n; ++i) occ[i] = 0;
-  for (int k = 1; k <= n; ++k) {
+  for (int i = lane; i < 128; i += 32) occ[w][i] = 0;
+  __syncwarp();
+  for (int k = 1 + lane; k <= n; k += 32) {
     const int s = slots[(size_t)b * n + (k - 1)];
-    occ[s] += 1;
-    occ[s + k + delta] += 1;
+    if (s < 2 * n - (k + delta)) {      // a start outside the pair's range counts nothing
+      atomicAdd(&occ[w][s], 1u);
+      atomicAdd(&occ[w][s + k + delta], 1u);
+    }
   }
-  __nv_bfloat16* x = X + (size_t)b * K1;
-  for (int i = 0; i < K1; ++i) x[i] = __float2bfloat16(i < 2 * n ? (float)occ[i] : 0.f);
+  __syncwarp();
+  for (int c = lane * 4; c < K1; c += 128) {
+    unsigned short h[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      h[i] = __bfloat16_as_ushort(__float2bfloat16((c + i < 2 * n) ? (float)occ[w][c + i] : 0.f));
+    *(uint2*)(X + (size_t)b * K1 + c) =
+        make_uint2((unsigned)h[0] | ((unsigned)h[1] << 16), (unsigned)h[2] | ((unsigned)h[3] << 16));
+  }
 }
 
 // out[c] += sum over rows of in[r][c] (bias gradients).
@@ -183,40 +199,98 @@ cudaError_t refresh_transposed(Mlp& m, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t gemm_tc(const TcGemmArgs& g, cudaStream_t s) {
-  if (g.M % kTcBM || g.N % kTcBN || g.K % kTcBK) return cudaErrorInvalidValue;
+// The driver's tensor-map encoder, found through the runtime (no link
+// against the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+  }
+  return fn;
+}
+
+// 2D tensor map of a row-major [rows][cols] matrix of bf16 (esize 2) or
+// fp32 (esize 4), box [box_rows][128 bytes], 128-byte swizzle.
+static bool encode_map(CUtensorMap* map, const void* ptr, int esize, int rows, int cols,
+                       int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * esize};
+  const cuuint32_t box[2] = {(cuuint32_t)(128 / esize), (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+             2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static bool make_tc_maps(Mlp& m) {
+  return encode_map(&m.tmA[0], m.X, 2, m.max_batch, m.K1, kTcBM) &&
+         encode_map(&m.tmA[1], m.H1, 2, m.max_batch, kHidden, kTcBM) &&
+         encode_map(&m.tmA[2], m.H2, 2, m.max_batch, kHidden, kTcBM) &&
+         encode_map(&m.tmB[0], m.W1t, 2, kHidden, m.K1, kTcBN) &&
+         encode_map(&m.tmB[1], m.W2t, 2, kHidden, kHidden, kTcBN) &&
+         encode_map(&m.tmB[2], m.W3t, 2, m.NMp, kHidden, kTcBN) &&
+         encode_map(&m.tmC[0], m.H1, 2, m.max_batch, kHidden, 32) &&
+         encode_map(&m.tmC[1], m.H2, 2, m.max_batch, kHidden, 32) &&
+         encode_map(&m.tmC[2], m.Z, 4, m.max_batch, m.NMp, 32);
+}
+
+// C = A B^T + bias on tcgen05: bf16 = 1 writes bf16(relu(.)), 0 writes fp32.
+cudaError_t gemm_tc(const TcGemmArgs& g, const CUtensorMap& amap, const CUtensorMap& bmap,
+                    const CUtensorMap& cmap, int bf16, cudaStream_t s) {
+  if (g.M % kTcBM || g.N % kTcBN || g.K % kTcBK || g.K > kTcMaxK || g.M <= 0)
+    return cudaErrorInvalidValue;
   static bool attr = false;
+  static int sms = 0;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kTcSmem);
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<1>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gemm_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kTcSmem);
     if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     attr = true;
   }
-  gemm_tc_kernel<<<dim3(g.N / kTcBN, g.M / kTcBM), 128, kTcSmem, s>>>(g);
+  // one CTA per SM, a whole number of CTAs per 256-wide column tile
+  const int NT = g.N / kTcBN, MT = g.M / kTcBM;
+  int per = sms / NT;
+  if (per < 1) per = 1;
+  if (per > MT) per = MT;
+  if (bf16)
+    gemm_tc_kernel<1><<<per * NT, kTcThreads, kTcSmem, s>>>(amap, bmap, cmap, g);
+  else
+    gemm_tc_kernel<0><<<per * NT, kTcThreads, kTcSmem, s>>>(amap, bmap, cmap, g);
   return cudaGetLastError();
 }
 
 // Forward pass for B (multiple of 128) states whose slots are already in
 // m.slots: X, H1, H2 (bf16) and Z (fp32 logits).
 cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s) {
-  mlp_inputs_kernel<<<(B + 127) / 128, 128, 0, s>>>(m.slots, B, m.n, m.delta, m.K1, m.X);
+  mlp_inputs_kernel<<<(B + 7) / 8, 256, 0, s>>>(m.slots, B, m.n, m.delta, m.K1, m.X);
   if (m.use_tc) {
     cudaError_t e = cudaSuccess;
     if (m.wt_dirty) e = refresh_transposed(m, s);
     if (e != cudaSuccess) return e;
     TcGemmArgs t;
     std::memset(&t, 0, sizeof(t));
-    t.M = B; t.N = kHidden; t.K = m.K1; t.A = m.X; t.lda = m.K1; t.Bt = m.W1t; t.ldb = m.K1;
-    t.C = m.H1; t.ldc = kHidden; t.bias = m.b1; t.relu_bf16 = 1; t.err = m.tc_err;
-    e = gemm_tc(t, s);
+    t.M = B; t.N = kHidden; t.K = m.K1; t.bias = m.b1; t.err = m.tc_err;
+    e = gemm_tc(t, m.tmA[0], m.tmB[0], m.tmC[0], 1, s);
     if (e != cudaSuccess) return e;
-    t.K = kHidden; t.A = m.H1; t.lda = kHidden; t.Bt = m.W2t; t.ldb = kHidden; t.C = m.H2;
-    t.bias = m.b2;
-    e = gemm_tc(t, s);
+    t.K = kHidden; t.bias = m.b2;
+    e = gemm_tc(t, m.tmA[1], m.tmB[1], m.tmC[1], 1, s);
     if (e != cudaSuccess) return e;
-    t.N = m.NMp; t.A = m.H2; t.Bt = m.W3t; t.ldb = kHidden; t.C = m.Z; t.ldc = m.NMp;
-    t.bias = m.b3; t.relu_bf16 = 0;
-    return gemm_tc(t, s);
+    t.N = m.NMp; t.bias = m.b3;
+    return gemm_tc(t, m.tmA[2], m.tmB[2], m.tmC[2], 0, s);
   }
   GemmArgs g;
   std::memset(&g, 0, sizeof(g));
@@ -366,6 +440,11 @@ int mlp_create(int variant, int n, int max_batch, uint64_t seed, Mlp** out) {
   m->tc_err = (unsigned*)(p + o_err);
   m->use_tc = 1;
   m->wt_dirty = 1;
+  if (!make_tc_maps(*m)) {          // the driver could not describe the buffers
+    cudaFree(p);
+    delete m;
+    return SK_ECUDA;
+  }
   // He-normal initial weights (input rows beyond 2n and move columns beyond
   // NM stay zero), zero biases
   std::vector<float> h(m->nparams, 0.f);

@@ -2,6 +2,7 @@
 // its training code (sk_mlp.cu) and the learned tempering chains
 // (sk_pt_learned.cu).
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -35,6 +36,11 @@ struct Mlp {
   int use_tc;                                // 1: forward on tcgen05 (default)
   int wt_dirty;                              // transposed copies need a refresh
   unsigned* tc_err;                          // error word of the tcgen05 GEMM
+  // TMA descriptors of the tcgen05 forward (128-byte swizzle): operands A =
+  // X, H1, H2 ([max_batch][K], boxes [128][64]) and B = W1t, W2t, W3t ([N][K],
+  // boxes [256][64]); results C = H1, H2 (bf16, boxes [32][64]) and Z (fp32,
+  // boxes [32][32])
+  CUtensorMap tmA[3], tmB[3], tmC[3];
   float* Z;
   float* loss;                               // [1]
   void* block;                               // one allocation holding all of the above

@@ -103,13 +103,15 @@ def test_learned_chains_are_exact(variant, n):
     assert abs(est / (oracle.backtrack_count(variant, n) / 2) - 1) < 0.02
 
 
-def test_tensor_memory_and_mma_sync_paths_agree():
+@pytest.mark.parametrize("variant,n,batch", [(1, 20, 4096), (1, 20, 65536), (0, 24, 40000)])
+def test_tensor_memory_and_mma_sync_paths_agree(variant, n, batch):
     # the two forward GEMM paths see the same bf16 operands; their fp32 sums
-    # differ only in accumulation order
-    n, variant = 20, 1
+    # differ only in accumulation order.  65536 and 40000 states give every
+    # CTA of the persistent tcgen05 GEMM several row tiles (the operand ring
+    # and both tensor-memory accumulators wrap around); 40000 is ragged.
     d = si.differences(variant, n)
-    model = sk.Mlp(variant, n, 4096, seed=6)
-    slots = si.random_slots(8, 4096, n, d)
+    model = sk.Mlp(variant, n, (batch + 127) // 128 * 128, seed=6)
+    slots = si.random_slots(8, batch, n, d)
     model.set_gemm(True)
     a = model.forward(slots)
     model.check()
