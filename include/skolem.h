@@ -66,6 +66,21 @@ enum { SK_COUNT_REFLECTIONS_IDENTIFIED = 0, SK_COUNT_ALL = 1 };
  * each prime by signed Montgomery steps (R = 2^32); compiled for three
  * moduli only (nprimes = 3). */
 enum { SK_ARITH_LIMBS = 0, SK_ARITH_MONTGOMERY = 1 };
+
+/* Symmetries used by the exact count.
+ * SK_SYMMETRY_NEGATION (default): Lemma 2.2 only -- the summand is unchanged
+ * when every x negates, so x_{max P} = +1 and 2^{2n-1} terms are summed.
+ * SK_SYMMETRY_NEGATION_EVEN: Lemmas 2.2 and 2.4 -- negating the x at the even
+ * positions multiplies the summand by s = (-1)^{e + o}, e = number of even
+ * positions in P, o = number of odd distances d_k (s = +1 exactly for Skolem
+ * n = 0,1, Langford n = 0,3 and hooked Skolem n = 2,3 (mod 4), the classes
+ * in which pairings exist).  s = -1: the sum is 0 and no term is evaluated.
+ * s = +1: one more variable is fixed to +1 (x_{2n-1} for Skolem and
+ * Langford, through the negation of the odd positions; x_{2n-2} for hooked
+ * Skolem, whose fixed position 2n+1 is odd) and 2^{2n-2} terms are summed;
+ * the result (residues, coefficient) is the same.  Needs n >= 4; smaller
+ * orders use SK_SYMMETRY_NEGATION (the report says which was used). */
+enum { SK_SYMMETRY_NEGATION = 0, SK_SYMMETRY_NEGATION_EVEN = 1 };
 #define SK_MAX_PRIMES 4
 
 typedef struct { uint64_t lo, hi; } sk_u128;   /* unsigned 128-bit integer */
@@ -92,6 +107,8 @@ typedef struct sk_count_opts {
   uint64_t max_chunks;         /* stop (status SK_OK, report->complete = 0)
                                   after this many new chunks; 0 = no limit */
   int arith;                   /* SK_ARITH_LIMBS (default) or SK_ARITH_MONTGOMERY */
+  int symmetry;                /* SK_SYMMETRY_NEGATION (default) or
+                                  SK_SYMMETRY_NEGATION_EVEN */
 } sk_count_opts;
 
 typedef struct sk_count_report {
@@ -100,8 +117,9 @@ typedef struct sk_count_report {
   uint64_t residues[SK_MAX_PRIMES]; /* H mod p_i, H = sum of Lemma 2.1 over the
                                        2^{2n-1} assignments with x_{max P} = +1 */
   sk_u128 coefficient;         /* pairings with reflections distinct */
-  uint64_t terms;              /* 2^{2n-1} */
-  uint64_t items;              /* work items (2^{2n-1-m}) */
+  uint64_t terms;              /* terms evaluated: 2^{2n-1} (Lemma 2.2),
+                                  2^{2n-2} (Lemma 2.4, s = +1) or 0 (s = -1) */
+  uint64_t items;              /* work items (terms / 2^m) */
   int walk_bits;               /* m */
   int inner_bits;              /* unrolled Gray bits */
   int arith;                   /* arithmetic form used */
@@ -110,6 +128,7 @@ typedef struct sk_count_report {
   int complete;                /* 1 when every chunk is done */
   double kernel_ms;            /* device time of the launches of this call */
   double wall_ms;              /* host time of the whole call */
+  int symmetry;                /* SK_SYMMETRY_* actually used */
 } sk_count_report;
 
 /* Exact count of `variant` of order n (Lemma 2.1 with Lemma 2.2, evaluated in

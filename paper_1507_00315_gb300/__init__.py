@@ -17,6 +17,7 @@ SKOLEM, LANGFORD, HOOKED = 0, 1, 2
 VARIANTS = {"skolem": SKOLEM, "langford": LANGFORD, "hooked": HOOKED}
 REFLECTIONS_IDENTIFIED, COUNT_ALL = 0, 1
 ARITH_LIMBS, ARITH_MONTGOMERY = 0, 1
+SYMMETRY_NEGATION, SYMMETRY_NEGATION_EVEN = 0, 1      # Lemma 2.2; Lemmas 2.2 + 2.4
 MAX_N = 28
 MAX_PRIMES = 4
 NOALLOC_MAX_ITEMS = 16384
@@ -49,7 +50,8 @@ class CountOpts(ctypes.Structure):
                 ("checkpoint_path", ctypes.c_char_p),
                 ("chunk_items", ctypes.c_uint64),
                 ("max_chunks", ctypes.c_uint64),
-                ("arith", ctypes.c_int)]
+                ("arith", ctypes.c_int),
+                ("symmetry", ctypes.c_int)]
 
 
 class CountReport(ctypes.Structure):
@@ -69,7 +71,8 @@ class CountReport(ctypes.Structure):
                 ("chunks_resumed", ctypes.c_uint64),
                 ("complete", ctypes.c_int),
                 ("kernel_ms", ctypes.c_double),
-                ("wall_ms", ctypes.c_double)]
+                ("wall_ms", ctypes.c_double),
+                ("symmetry", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         k = self.nprimes
@@ -79,7 +82,7 @@ class CountReport(ctypes.Structure):
                 "block_threads": self.block_threads, "grid": self.grid,
                 "chunks_total": self.chunks_total, "chunks_done": self.chunks_done,
                 "chunks_resumed": self.chunks_resumed, "complete": bool(self.complete),
-                "kernel_ms": self.kernel_ms, "wall_ms": self.wall_ms}
+                "kernel_ms": self.kernel_ms, "wall_ms": self.wall_ms, "symmetry": self.symmetry}
 
 
 class Job(ctypes.Structure):
@@ -231,7 +234,8 @@ def default_primes():
 
 
 def _opts(nprimes=0, primes=None, convention=REFLECTIONS_IDENTIFIED, walk_bits=0, block_threads=0,
-          grid=0, stream=None, checkpoint=None, chunk_items=0, max_chunks=0, arith=ARITH_LIMBS):
+          grid=0, stream=None, checkpoint=None, chunk_items=0, max_chunks=0, arith=ARITH_LIMBS,
+          symmetry=SYMMETRY_NEGATION):
     o = CountOpts()
     o.nprimes = nprimes
     for i, p in enumerate(primes or []):
@@ -245,6 +249,7 @@ def _opts(nprimes=0, primes=None, convention=REFLECTIONS_IDENTIFIED, walk_bits=0
     o.chunk_items = chunk_items
     o.max_chunks = max_chunks
     o.arith = arith
+    o.symmetry = symmetry
     return o
 
 
@@ -260,7 +265,8 @@ def count(variant, n: int) -> int:
 def count_ex(variant, n: int, **kw):
     """skolem_count_ex: returns (count or None if incomplete, report dict).
     Keywords: nprimes, primes, convention, walk_bits, block_threads, grid,
-    stream (int handle), checkpoint (path), chunk_items, max_chunks, arith."""
+    stream (int handle), checkpoint (path), chunk_items, max_chunks, arith,
+    symmetry (SYMMETRY_NEGATION or SYMMETRY_NEGATION_EVEN)."""
     o = _opts(**kw)
     out = U128()
     rep = CountReport()

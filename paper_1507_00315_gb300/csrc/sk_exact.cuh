@@ -62,10 +62,20 @@ struct Res4 {                    // residues of one work item
 // Parameters of one exact-count problem as the kernels see it.
 struct ExactJob {
   unsigned long long pres;   // bit i set iff position i+1 belongs to P
-  unsigned long long items;  // number of work items (2^{2n-1-m})
+  unsigned long long items;  // number of work items (2^{F-m}, F free bits)
   int m;                     // walk bits per item
   int job;                   // slot index of this job's residues
+  int fixed_bit;             // 0: none; else a free bit >= m held at +1 (Lemma
+                             // 2.4): item indices skip it
 };
+
+// Item index -> the free-bit pattern above the walk: a zero is inserted at
+// bit `hole` (the fixed variable), the bits at and above it move up by one.
+__host__ __device__ __forceinline__ unsigned long long insert_zero_bit(unsigned long long q,
+                                                                      int hole) {
+  const unsigned long long low = q & ((1ULL << hole) - 1);
+  return low | ((q >> hole) << (hole + 1));
+}
 
 // ------------------------------------------------------------ compile time
 

@@ -131,7 +131,9 @@ __device__ __forceinline__ void work_loop(const ExactJob& job, const Primes& P, 
     if (base >= count) break;
     const unsigned long long it = base + lane;
     if (it < count) {
-      const Res4 r = Item::eval(job, P, nprimes, item_lo + it, ws_col);
+      const unsigned long long q =
+          job.fixed_bit ? insert_zero_bit(item_lo + it, job.fixed_bit - job.m) : item_lo + it;
+      const Res4 r = Item::eval(job, P, nprimes, q, ws_col);
 #pragma unroll
       for (int i = 0; i < kMaxPrimes; ++i) {
         if (i >= nprimes) break;

@@ -105,6 +105,9 @@ int default_walk_bits(int n) {
 
 struct Plan {
   int variant, n, delta, m, U, nprimes, block_threads, grid, arith;
+  int symmetry;     // SK_SYMMETRY_* used
+  int sign;         // Lemma 2.4 sign s (+1 / -1) when symmetry uses it
+  int fixed_bit;    // free bit held at +1 by Lemma 2.4 (0: none)
   unsigned long long pres, items;
   uint64_t primes[kMaxPrimes];
   Primes P;
@@ -130,9 +133,33 @@ static int make_plan(int variant, int n, const sk_count_opts* o, Plan* pl) {
     pl->m = default_walk_bits(n);
     if (pl->m > mmax) pl->m = mmax;
   }
-  if (pl->m < pl->U || pl->m > F || pl->m > mmax || F - pl->m > 56) return SK_EINVAL;
-  pl->items = 1ULL << (F - pl->m);
   pl->pres = position_mask(variant, n);
+  // Lemma 2.4: negating the even positions multiplies the summand by
+  // s = (-1)^{#even positions in P + #odd d_k}.  With s = +1 the summand is
+  // constant on {X, X with the odd (Skolem, Langford) or even (hooked; its
+  // fixed position 2n+1 is odd) positions negated}, so one more free
+  // variable -- the highest of that parity -- is held at +1 and the sum
+  // doubled; with s = -1 the sum is 0.
+  const int sym = o ? o->symmetry : SK_SYMMETRY_NEGATION;
+  if (sym != SK_SYMMETRY_NEGATION && sym != SK_SYMMETRY_NEGATION_EVEN) return SK_EINVAL;
+  pl->symmetry = SK_SYMMETRY_NEGATION;
+  pl->sign = 1;
+  pl->fixed_bit = 0;
+  int Feff = F;
+  if (sym == SK_SYMMETRY_NEGATION_EVEN && n >= 4) {
+    int e = 0, odd_d = 0;
+    for (int i = 0; i < 64; ++i)
+      if (((pl->pres >> i) & 1ULL) && (i & 1)) ++e;     // bit i = position i+1
+    for (int k = 1; k <= n; ++k) odd_d += (k + pl->delta) & 1;
+    pl->symmetry = SK_SYMMETRY_NEGATION_EVEN;
+    pl->sign = ((e + odd_d) & 1) ? -1 : 1;
+    pl->fixed_bit = (variant == SK_HOOKED) ? 2 * n - 3 : 2 * n - 2;
+    Feff = F - 1;
+    if (!(o && o->walk_bits) && pl->m > pl->fixed_bit) pl->m = pl->fixed_bit;
+    if (pl->m > pl->fixed_bit) return SK_EINVAL;        // the fixed bit must lie above the walk
+  }
+  if (pl->m < pl->U || pl->m > F || pl->m > mmax || F - pl->m > 56) return SK_EINVAL;
+  pl->items = 1ULL << (Feff - pl->m);
   pl->block_threads = (o && o->block_threads) ? o->block_threads : 256;
   if (pl->block_threads < 32 || pl->block_threads > 256 || (pl->block_threads & 31)) return SK_EINVAL;
   pl->grid = (o && o->grid > 0) ? o->grid : 0;
@@ -166,6 +193,7 @@ static int run_chunk(const Plan& pl, unsigned long long lo, unsigned long long h
   L.job.items = pl.items;
   L.job.m = pl.m;
   L.job.job = 0;
+  L.job.fixed_bit = pl.fixed_bit;
   L.P = pl.P;
   L.nprimes = pl.nprimes;
   L.item_lo = lo;
@@ -211,7 +239,9 @@ static std::string ckpt_header(const Plan& pl, unsigned long long chunk_items,
                 (unsigned long long)pl.primes[1], (unsigned long long)pl.primes[2],
                 (unsigned long long)(pl.nprimes > 3 ? pl.primes[3] : 0), pl.items, chunk_items,
                 nchunks);
-  return std::string(buf);
+  std::string h(buf);
+  if (pl.symmetry == SK_SYMMETRY_NEGATION_EVEN) h += " s=lemma2.4";
+  return h;
 }
 
 // Reads an existing checkpoint; a missing file is an empty checkpoint.  A
@@ -324,6 +354,25 @@ int count_impl(int variant, int n, const sk_count_opts* o, sk_u128* out, sk_coun
     return SK_EINVAL;
   st = check_device();
   if (st) return st;
+  if (pl.sign < 0) {
+    // Lemma 2.4 with s = -1: the sum is 0 (a zero class); nothing to evaluate
+    if (rep) {
+      std::memset(rep, 0, sizeof(*rep));
+      rep->nprimes = pl.nprimes;
+      for (int i = 0; i < pl.nprimes; ++i) rep->primes[i] = pl.primes[i];
+      rep->walk_bits = pl.m;
+      rep->inner_bits = pl.U;
+      rep->arith = pl.arith;
+      rep->block_threads = pl.block_threads;
+      rep->grid = pl.grid;
+      rep->complete = 1;
+      rep->symmetry = pl.symmetry;
+      rep->wall_ms =
+          std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (out) *out = sk_u128{0, 0};
+    return SK_OK;
+  }
   cudaStream_t stream = (o && o->stream) ? (cudaStream_t)o->stream : nullptr;
   bool own_stream = false;
   if (!stream) {
@@ -402,6 +451,8 @@ int count_impl(int variant, int n, const sk_count_opts* o, sk_u128* out, sk_coun
   if (st) return st;
   const bool complete = done_total == nchunks;
   unmont(pl, H);
+  if (pl.symmetry == SK_SYMMETRY_NEGATION_EVEN)      // Lemma 2.4, s = +1: H = 2 H'
+    for (int i = 0; i < pl.nprimes; ++i) H[i] = (H[i] * 2) % pl.primes[i];
   sk_u128 coeff = {0, 0};
   if (complete) {
     st = crt_coefficient(n, pl.nprimes, pl.primes, H, &coeff);
@@ -415,8 +466,9 @@ int count_impl(int variant, int n, const sk_count_opts* o, sk_u128* out, sk_coun
       rep->residues[i] = complete ? H[i] : 0;
     }
     rep->coefficient = coeff;
-    rep->terms = 1ULL << (2 * n - 1);
+    rep->terms = pl.items << pl.m;
     rep->items = pl.items;
+    rep->symmetry = pl.symmetry;
     rep->walk_bits = pl.m;
     rep->inner_bits = pl.U;
     rep->arith = pl.arith;

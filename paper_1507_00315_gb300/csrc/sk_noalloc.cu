@@ -104,6 +104,7 @@ extern "C" int skolem_item_residues_noalloc(int variant, int n, int m, uint64_t 
   L.job.items = items;
   L.job.m = m;
   L.job.job = 0;
+  L.job.fixed_bit = 0;
   L.P = P;
   L.nprimes = k;
   L.item_lo = q_lo;

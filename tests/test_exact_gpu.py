@@ -177,3 +177,45 @@ def test_checkpoint_resume(tmp_path):
     with pytest.raises(sk.SkolemError) as e:
         sk.count_ex(SK, 12, checkpoint=path, chunk_items=1 << 10, walk_bits=9)
     assert e.value.status == sk.SK_ECKPT
+
+
+@pytest.mark.parametrize("variant", [SK, LA, HO])
+def test_lemma_2_4_option_same_result_half_the_terms(variant):
+    # Lemmas 2.2 + 2.4: the same residues H mod p and count as Lemma 2.2
+    # alone; half the terms in the existence classes, none in the zero
+    # classes; orders below 4 keep Lemma 2.2 alone.
+    for n in range(1, 18):
+        c0, r0 = sk.count_ex(variant, n, nprimes=4, convention=sk.COUNT_ALL)
+        c1, r1 = sk.count_ex(variant, n, nprimes=4, convention=sk.COUNT_ALL,
+                             symmetry=sk.SYMMETRY_NEGATION_EVEN)
+        assert c1 == c0 and r1["residues"] == r0["residues"], (variant, n)
+        if n < 4:
+            assert r1["symmetry"] == sk.SYMMETRY_NEGATION and r1["terms"] == r0["terms"]
+            continue
+        assert r1["symmetry"] == sk.SYMMETRY_NEGATION_EVEN
+        assert r1["terms"] == (r0["terms"] // 2 if c0 else 0), (variant, n)
+
+
+def test_lemma_2_4_mid_size_against_the_paper(skolem_table, langford_table):
+    for variant, n, table in ((SK, 20, skolem_table), (LA, 19, langford_table)):
+        c, rep = sk.count_ex(variant, n, nprimes=4, symmetry=sk.SYMMETRY_NEGATION_EVEN)
+        assert c == table[n] and rep["terms"] == 1 << (2 * n - 2)
+    # a zero class of the same size costs nothing
+    c, rep = sk.count_ex(SK, 19, symmetry=sk.SYMMETRY_NEGATION_EVEN)
+    assert c == 0 and rep["terms"] == 0
+
+
+def test_lemma_2_4_checkpoint(tmp_path):
+    path = str(tmp_path / "ck24.txt")
+    kw = dict(convention=sk.COUNT_ALL, chunk_items=1 << 8, walk_bits=9,
+              symmetry=sk.SYMMETRY_NEGATION_EVEN)
+    full, _ = sk.count_ex(HO, 14, convention=sk.COUNT_ALL)
+    c1, r1 = sk.count_ex(HO, 14, checkpoint=path, max_chunks=3, **kw)
+    assert c1 is None and r1["chunks_done"] == 3
+    c2, r2 = sk.count_ex(HO, 14, checkpoint=path, **kw)
+    assert c2 == full and r2["chunks_resumed"] == 3
+    # the same order without Lemma 2.4 is another job
+    with pytest.raises(sk.SkolemError) as e:
+        sk.count_ex(HO, 14, convention=sk.COUNT_ALL, checkpoint=path, chunk_items=1 << 8,
+                    walk_bits=9)
+    assert e.value.status == sk.SK_ECKPT

@@ -151,6 +151,58 @@ def test_lemma_2_4_even_negation():
             assert a == (b if n % 4 in (0, 1) else -b)
 
 
+def _lemma_2_4_sign(variant, n):
+    # (-1)^{#even positions in P + #odd distances d_k}
+    _, pos, d = oracle.layout(variant, n)
+    e = sum(1 for q in pos if q % 2 == 0)
+    o = sum(1 for x in d if x % 2 == 1)
+    return -1 if (e + o) % 2 else 1
+
+
+@pytest.mark.parametrize("variant", [SK, LA, HO])
+def test_lemma_2_4_sign_all_variants(variant):
+    # Negating the even positions multiplies the summand by s: the
+    # correlations at an odd distance change sign, those at an even distance
+    # do not, and prod x changes by (-1)^{#even positions}.  s = +1 exactly in
+    # the classes where pairings exist (Skolem 0,1, Langford 0,3, hooked 2,3
+    # mod 4).
+    rng = random.Random(5 + variant)
+    exist = {SK: (0, 1), LA: (0, 3), HO: (2, 3)}[variant]
+    for n in range(3, 13):
+        s = _lemma_2_4_sign(variant, n)
+        assert (s == 1) == (n % 4 in exist), (variant, n)
+        span, _, _ = oracle.layout(variant, n)
+        for _ in range(10):
+            x = _rand_x(rng, span)
+            y = [0] + [(-v if i % 2 == 0 else v) for i, v in enumerate(x[1:], start=1)]
+            assert oracle.summand(variant, n, y) == s * oracle.summand(variant, n, x)
+
+
+@pytest.mark.parametrize("variant,n", [(SK, 8), (SK, 9), (SK, 6), (LA, 7), (LA, 8), (LA, 5),
+                                       (HO, 6), (HO, 7), (HO, 8)])
+def test_lemma_2_4_fixed_variable(variant, n):
+    # With x_{max P} = +1 (Lemma 2.2), also holding one more variable at +1 --
+    # position 2n-1 (Skolem, Langford) or 2n-2 (hooked) -- and multiplying by
+    # 1 + s gives the half sum: the blocks with that variable at -1 add up to
+    # s times the others.
+    p = (1 << 61) - 1
+    s = _lemma_2_4_sign(variant, n)
+    fixed_pos = 2 * n - 2 if variant == HO else 2 * n - 1
+    m = 4
+    hole = fixed_pos - 1 - m                 # bit of the block index q
+    nfree = 2 * n - 1
+    kept = dropped = 0
+    for q in range(1 << (nfree - m)):
+        v = oracle.partial_sum_mod(variant, n, m, q, p)
+        if (q >> hole) & 1:
+            dropped = (dropped + v) % p
+        else:
+            kept = (kept + v) % p
+    half = oracle.signed_sum(variant, n, half=True) % p
+    assert dropped == (s * kept) % p
+    assert ((1 + s) * kept) % p == half
+
+
 def test_summand_brute_expansion():
     # The summand is sign(X) * prod_i sum_k x_k x_{k+i}; check it against the
     # expansion of F(4, X) printed in Sec. 2.1 at random points.
