@@ -119,8 +119,11 @@ int batch_primes(const sk_batch_opts* o, int* k, uint64_t* pv, Primes* P) {
 
 int delta_of(int variant) { return variant == SK_LANGFORD ? 1 : 0; }
 
-// Times the exact-form kernel of one (variant, n) on the first items (a fixed
-// number of terms for every candidate) and keeps the fastest configuration.
+// Times the exact-form kernel of one (variant, n) on its first items -- one
+// full wave, SMs x 512 resident threads with one item each, so every
+// candidate is timed in the steady state of a long launch -- and keeps the
+// fastest configuration; the default one unless another is at least 3 %
+// faster (single timings of this length vary by about 1 %).
 int tune_impl(int variant, int n, const sk_batch_opts* o, sk_tune_result* out) {
   if (variant < SK_SKOLEM || variant > SK_HOOKED || n < 1 || n > kMaxN || !out) return SK_EINVAL;
   int k = 0;
@@ -154,14 +157,16 @@ int tune_impl(int variant, int n, const sk_batch_opts* o, sk_tune_result* out) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  Tuned best;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned long long wave = (unsigned long long)(sms > 0 ? sms : 1) * 512ULL;
+  Tuned best, dflt;
   int cand = 0;
   const int bts[2] = {128, 256};
   for (int m : ms) {
     const unsigned long long items = 1ULL << (F - m);
-    const int lg = 33 - m;                       // 2^33 terms per sample at most
-    const unsigned long long sample = lg <= 0 ? 1ULL : (lg >= 62 ? items
-                                          : ((1ULL << lg) < items ? (1ULL << lg) : items));
+    const unsigned long long sample = wave < items ? wave : items;
     for (int bt : bts) {
       ExactLaunch L;
       std::memset(&L, 0, sizeof(L));
@@ -189,9 +194,11 @@ int tune_impl(int variant, int n, const sk_batch_opts* o, sk_tune_result* out) {
       ++cand;
       const double rate = (double)sample * (double)(1ULL << m) / (ms_t * 1e-3);
       if (rate > best.rate) { best.rate = rate; best.m = m; best.bt = bt; }
+      if (m == m0 && bt == 256) { dflt.rate = rate; dflt.m = m; dflt.bt = bt; }
     }
     if (st) break;
   }
+  if (dflt.rate > 0 && best.rate < 1.03 * dflt.rate) best = dflt;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(d);
