@@ -311,10 +311,11 @@ void orc_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out)
 
 /* ----------------------------------------- O3: Algorithm 2 (tempering) */
 
-/* Random-number streams (one Philox call each):
+/* Random-number streams (one Philox block each):
  *   init   : counter (k, rung, ladder, 1) word 0 -> start slot of pair k
  *   move   : counter (t, rung, ladder, 2) words 0,1,2 -> pair, slot, accept
- *   swap   : counter (t, j,    ladder, 3) word 0 -> exchange of (j, j+1)
+ *   swap   : counter (t, j,    ladder, 2) word 3 -> exchange of (j, j+1)
+ *            (the word rung j's move leaves unused)
  * key = (seed & 0xffffffff, seed >> 32). */
 
 static uint64_t accept_threshold(double x)   /* x = beta * dE > 0 */
@@ -415,10 +416,11 @@ int orc_pt_run(int variant, int n, int M, const double *beta, int L, uint64_t it
                 }
             }
             for (int j = (int)(t & 1); j + 1 < M; j += 2) {   /* exchanges */
-                uint32_t c[4] = {(uint32_t)t, (uint32_t)j, (uint32_t)l, 3u}, r[4];
+                /* the fourth word of rung j's block of this iteration */
+                uint32_t c[4] = {(uint32_t)t, (uint32_t)j, (uint32_t)l, 2u}, r[4];
                 orc_philox4x32_10(c, key, r);
                 int de = conf[j].E - conf[j + 1].E;
-                int accept = (de <= 0) || ((uint64_t)r[0] < tswap[j * (bins + 1) + de]);
+                int accept = (de <= 0) || ((uint64_t)r[3] < tswap[j * (bins + 1) + de]);
                 if (accept) {
                     pt_conf tmp = conf[j];
                     conf[j] = conf[j + 1];

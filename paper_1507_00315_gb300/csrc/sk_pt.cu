@@ -62,10 +62,12 @@ __global__ void __launch_bounds__(128, 7)
           if (hist[i]) { atomicAdd(&hist_g[i], (unsigned long long)hist[i]); hist[i] = 0; }
         __syncwarp();
       }
+      unsigned xw = 0;                                 // word 3 of this lane's move block
       if (active) {
         if (t >= p.burnin) hist[r * nb + E] += 1;
         const uint4 w = philox4x32_10(make_uint4(tt, (unsigned)r, (unsigned)ladder, 2u), p.key0,
                                       p.key1);
+        xw = w.w;
         const int k = 1 + (int)__umulhi(w.x, (unsigned)n);
         const int d = k + p.delta;
         const int L = bins - d;
@@ -96,13 +98,12 @@ __global__ void __launch_bounds__(128, 7)
       }
       // exchanges: lane j acts for rung j
       const int Er = __shfl_sync(0xffffffffu, E, lor);
+      const unsigned xr = __shfl_sync(0xffffffffu, xw, lor);   // word 3 of rung `lane`'s block
       const int En = __shfl_down_sync(0xffffffffu, Er, 1);
       int dec = 0;
       if (lane + 1 < M && (lane & 1) == (int)(tt & 1u)) {
-        const uint4 w = philox4x32_10(make_uint4(tt, (unsigned)lane, (unsigned)ladder, 3u),
-                                      p.key0, p.key1);
         const int de = Er - En;
-        dec = (de <= 0 || (unsigned long long)w.x < __ldg(&tswap[lane * nb + de])) ? 1 : 0;
+        dec = (de <= 0 || (unsigned long long)xr < __ldg(&tswap[lane * nb + de])) ? 1 : 0;
         if (dec) accs[lane] += 1;
       }
       const int lor_down = __shfl_down_sync(0xffffffffu, lor, 1);

@@ -11,9 +11,11 @@
 //
 // Random numbers: Philox-4x32-10 (Salmon et al., SC'11), one call per
 // (counter, key): counter (k, rung, ladder, 1) for the start slot of pair k,
-// (t, rung, ladder, 2) for the move at iteration t of the configuration at
-// that rung (word 0: pair, word 1: slot, word 2: acceptance), (t, j, ladder,
-// 3) word 0 for the exchange of rungs (j, j+1); key = the 64-bit seed.
+// (t, rung, ladder, 2) for iteration t at that rung -- word 0: pair, word 1:
+// slot, word 2: acceptance of the move of the configuration at the rung,
+// word 3: acceptance of the exchange of rungs (rung, rung+1); key = the
+// 64-bit seed.  (One block per rung and iteration: the exchange needs no
+// call of its own.)
 // Acceptance compares a 32-bit word w with a threshold T = ceil(p 2^32)
 // (T = 2^32: always), i.e. accept iff w / 2^32 < p.
 #pragma once
