@@ -268,6 +268,16 @@ def run_extra(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# 32-bit integer operations of one Metropolis iteration of one chain in
+# Algorithm 2 (plain proposal): one Philox-4x32-10 block (10 rounds of two
+# 32x32->64 products, counted as two operations each, two three-input xors
+# and two key additions: 80); the move (pair and slot by two multiply-highs,
+# the skip of the current slot, four occupancy updates with their empty-bin
+# tests, the energy change, the threshold test, the slot write or the undo:
+# 18); the histogram count (3); the exchange decision, made for half of the
+# rungs per iteration (energy difference, threshold test, label update: 2).
+PT_OPS_PER_LANE_ITERATION = 80 + 18 + 3 + 2
+
 EXACT_S = {16: 700078384, 20: 5717789399488, 24: 102388058845620672}
 EXACT_L = {16: 326721800, 20: 2636337861200, 24: 46845158056515936}
 
@@ -311,8 +321,19 @@ def run_pt_bench(args, sk, sh):
         for prop in ("plain", "learned"):
             ok = [r for r in rows if r["proposal"] == prop and abs(r["rel_error"]) < 0.01]
             summary[f"{case} {prop}: GPU ms to |error| < 1%"] = min((r["gpu_ms"] for r in ok), default=None)
+    # roofline of the plain tempering kernel: its longest run
+    case, big = max(((c, r) for c, rows in out.items() for r in rows if r["proposal"] == "plain"),
+                    key=lambda x: x[1]["gpu_ms"])
+    rate = 4096 * 32 * big["iterations"] / (big["gpu_ms"] * 1e-3)
+    peak = sk.int32_peak(1)[0] / 1e12
+    achieved = PT_OPS_PER_LANE_ITERATION * rate / 1e12
+    roofline = {"bound": "alu", "kernel": f"pt_kernel ({case}, {big['iterations']} iterations)",
+                "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": None, "ops_per_lane_iteration": PT_OPS_PER_LANE_ITERATION,
+                "lane_iterations_per_s": rate,
+                "peak_source": "measured: sk_int32_peak mode 1 (multiply-add / lop3 mix), same run"}
     return {"metric": "PT relative error vs GPU time, learned vs plain proposal",
-            "summary": summary,
+            "summary": summary, "roofline": roofline,
             "config": {"workload": "32 temperatures x 4096 ladders, Skolem / Langford n=16..24",
                        "training": f"{args.pt_samples} plain-PT states, 1 epoch, Adam 1e-3"},
             "unit": "relative error", "results": out}

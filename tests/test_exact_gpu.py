@@ -219,3 +219,19 @@ def test_lemma_2_4_checkpoint(tmp_path):
         sk.count_ex(HO, 14, convention=sk.COUNT_ALL, checkpoint=path, chunk_items=1 << 8,
                     walk_bits=9)
     assert e.value.status == sk.SK_ECKPT
+
+
+@pytest.mark.parametrize("variant", [SK, LA, HO])
+def test_every_order_one_item_vs_oracle(variant):
+    # Each (delta, n) kernel has its own compile-time plan (grouping, tail or
+    # digit form, product shape): one work item of every order 4..28, both
+    # arithmetic forms, against the oracle's block sum.
+    primes = sk.default_primes()[:4]
+    for n in range(4, 29):
+        F = 2 * n - 1
+        m = min(9, F)
+        q = (0x2D5A3C6B9E1F4 * (n + 7)) % (1 << (F - m))
+        a = sk.item_residues(variant, n, m, q, 1, primes, arith=sk.ARITH_LIMBS)[0]
+        b = sk.item_residues(variant, n, m, q, 1, primes[:3], arith=sk.ARITH_MONTGOMERY)[0]
+        want = [oracle.partial_sum_mod(variant, n, m, q, p) for p in primes]
+        assert a == want and b == want[:3], (variant, n, q, a, b, want)
