@@ -54,7 +54,8 @@ struct MoveTable {
 // dE of moving pair k (start s_k) to start s (d = k + delta), from the bin
 // occupancies occ of the configuration: taking the pair out empties the bins
 // it was alone in; putting it back fills the empty bins it lands on.
-__device__ __forceinline__ int move_delta_e(const unsigned char* occ, int sk, int d, int s) {
+template <class Occ>
+__device__ __forceinline__ int move_delta_e(const Occ* occ, int sk, int d, int s) {
   const int out = (occ[sk] == 1) + (occ[sk + d] == 1);
   const int o1 = occ[s] - (s == sk) - (s == sk + d);
   const int o2 = occ[s + d] - (s + d == sk) - (s + d == sk + d);

@@ -75,24 +75,26 @@ __global__ void __launch_bounds__(128, 7)
           const int s_old = slot[k * 32 + lane];
           int s_new = (int)__umulhi(w.y, (unsigned)(L - 1));
           if (s_new >= s_old) ++s_new;
-          const int E0 = E;
+          // dE from the four occupancies read at once: taking the pair out
+          // empties the bins it was alone in; putting it back fills the
+          // empty bins it lands on (s_new != s_old; a new bin may be the old
+          // pair's other bin)
           unsigned char* o1 = &occ[s_old * 32 + lane];
           unsigned char* o2 = &occ[(s_old + d) * 32 + lane];
           unsigned char* o3 = &occ[s_new * 32 + lane];
           unsigned char* o4 = &occ[(s_new + d) * 32 + lane];
-          if (--(*o1) == 0) ++E;
-          if (--(*o2) == 0) ++E;
-          if ((*o3)++ == 0) --E;
-          if ((*o4)++ == 0) --E;
-          const int dE = E - E0;
+          const int a1 = *o1, a2 = *o2, a3 = *o3, a4 = *o4;
+          const int b3 = a3 - (s_new == s_old + d);
+          const int b4 = a4 - (s_new + d == s_old);
+          const int dE = (a1 == 1) + (a2 == 1) - (b3 == 0) - (b4 == 0);
           if (dE <= 0 || (unsigned long long)w.z < __ldg(&tmove[r * 3 + dE])) {
+            --(*o1);                                 // one after the other: bins may coincide
+            --(*o2);
+            ++(*o3);
+            ++(*o4);
+            E += dE;
             slot[k * 32 + lane] = (unsigned char)s_new;
             accm[r] += 1;
-          } else {                                   // undo
-            if (--(*o3) == 0) ++E;
-            if (--(*o4) == 0) ++E;
-            if ((*o1)++ == 0) --E;
-            if ((*o2)++ == 0) --E;
           }
         }
       }

@@ -10,6 +10,7 @@
 // logits for the next draw.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -38,35 +39,64 @@ struct LearnedDev {
   const unsigned long long* tswap;   // [M][nb]
 };
 
-__device__ __forceinline__ void load_state(const unsigned char* sl, int n, int delta,
-                                           unsigned char* s_slot, unsigned char* s_occ, int lane) {
-  for (int i = lane; i < 2 * n; i += 32) s_occ[i] = 0;
-  __syncwarp();
-  if (lane == 0)
-    for (int k = 1; k <= n; ++k) {
-      const int s = sl[k - 1];
-      s_slot[k] = (unsigned char)s;
-      s_occ[s] += 1;
-      s_occ[s + k + delta] += 1;
+// Per-block tables of the move layout: the pair k and the start slot of
+// every move m (moves of pair k are off[k] .. off[k+1]-1), so a lane tests
+// "m is a valid move" (its slot is not the pair's current one) with two
+// shared-memory loads.
+constexpr int kMaxMoves = 2560;        // sum_k (2n - d_k) for n <= kPtMaxN
+struct MoveMaps {
+  unsigned char k[kMaxMoves];
+  unsigned char s[kMaxMoves];
+};
+
+__device__ __forceinline__ void build_move_maps(const MoveTable& mt, MoveMaps& mm) {
+  for (int m = threadIdx.x; m < mt.NM; m += blockDim.x) {
+    int lo = 1, hi = mt.n;                 // the pair with off[k] <= m < off[k+1]
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (mt.off[mid] <= m) lo = mid;
+      else hi = mid - 1;
     }
+    mm.k[m] = (unsigned char)lo;
+    mm.s[m] = (unsigned char)(m - mt.off[lo]);
+  }
+}
+
+// One warp loads a configuration: lane k-1 takes pair k (slot, and its two
+// bins into the occupancy counts when occ is given).
+__device__ __forceinline__ void load_state(const unsigned char* sl, int n, int delta,
+                                           unsigned char* s_slot, int* occ, int lane) {
+  if (occ)
+    for (int i = lane; i < 2 * n; i += 32) occ[i] = 0;
+  __syncwarp();
+  for (int k = 1 + lane; k <= n; k += 32) {
+    const int s = sl[k - 1];
+    s_slot[k] = (unsigned char)s;
+    if (occ) {
+      atomicAdd(&occ[s], 1);
+      atomicAdd(&occ[s + k + delta], 1);
+    }
+  }
   __syncwarp();
 }
 
-// log sum exp of the logits z over the valid moves of the state in smem.
-__device__ float valid_lse(const float* z, const MoveTable& mt, const unsigned char* s_slot,
-                           int lane) {
+__device__ __forceinline__ bool valid_move(const MoveMaps& mm, const unsigned char* s_slot,
+                                           int m) {
+  return mm.s[m] != s_slot[mm.k[m]];
+}
+
+// log sum exp of the logits z over the valid moves of the state in s_slot:
+// a coalesced pass for the maximum, a second (from L1) for the sum.
+__device__ float valid_lse(const float* z, const MoveMaps& mm, int NM,
+                           const unsigned char* s_slot, int lane) {
   float mx = -INFINITY;
-  for (int m = lane, k = 1; m < mt.NM; m += 32) {
-    while (m >= mt.off[k + 1]) ++k;
-    if (m - mt.off[k] != s_slot[k]) mx = fmaxf(mx, z[m]);
-  }
+  for (int m = lane; m < NM; m += 32)
+    if (valid_move(mm, s_slot, m)) mx = fmaxf(mx, z[m]);
   mx = warp_max(mx);
   float sum = 0.f;
-  for (int m = lane, k = 1; m < mt.NM; m += 32) {
-    while (m >= mt.off[k + 1]) ++k;
-    if (m - mt.off[k] != s_slot[k]) sum += expf(z[m] - mx);
-  }
-  return mx + logf(warp_sum(sum));
+  for (int m = lane; m < NM; m += 32)
+    if (valid_move(mm, s_slot, m)) sum += __expf(z[m] - mx);
+  return mx + __logf(warp_sum(sum));
 }
 
 __global__ void lt_init_kernel(LearnedDev d) {
@@ -92,116 +122,117 @@ __global__ void lt_init_kernel(LearnedDev d) {
 }
 
 // After a forward pass of the current states: keep their logits and lse.
-__global__ void __launch_bounds__(256) lt_keep_kernel(LearnedDev d, MoveTable mt, const float* Z) {
-  __shared__ unsigned char s_occ[8][2 * kPtMaxN];
-  __shared__ unsigned char s_slot[8][kPtMaxN + 1];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, c = blockIdx.x * 8 + w;
-  if (c >= d.B) return;
-  load_state(d.slots + (size_t)c * d.n, d.n, d.delta, s_slot[w], s_occ[w], lane);
-  const float* z = Z + (size_t)c * d.NMp;
-  float* zc = d.Zcur + (size_t)c * d.NMp;
-  for (int m = lane; m < d.NMp; m += 32) zc[m] = z[m];
-  const float l = valid_lse(z, mt, s_slot[w], lane);
-  if (lane == 0) d.lse[c] = l;
+__global__ void __launch_bounds__(256, 4) lt_keep_kernel(LearnedDev d, MoveTable mt, const float* Z) {
+  __shared__ MoveMaps mm;
+  __shared__ unsigned char s_slot[8][kPtMaxN + 8];
+  build_move_maps(mt, mm);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c = blockIdx.x * 8 + w; c < d.B; c += gridDim.x * 8) {
+    load_state(d.slots + (size_t)c * d.n, d.n, d.delta, s_slot[w], nullptr, lane);
+    const float* z = Z + (size_t)c * d.NMp;
+    float* zc = d.Zcur + (size_t)c * d.NMp;
+    for (int m = lane; m < d.NMp; m += 32) zc[m] = z[m];
+    const float l = valid_lse(z, mm, mt.NM, s_slot[w], lane);
+    if (lane == 0) d.lse[c] = l;
+    __syncwarp();
+  }
 }
 
 // Statistics of iteration t, then a move drawn from the current softmax; the
-// proposed configuration goes to `prop_slots` (the network's input).
-__global__ void __launch_bounds__(256) lt_propose_kernel(LearnedDev d, MoveTable mt, unsigned t,
+// proposed configuration goes to `prop_slots` (the network's input).  The
+// draw is an inverse CDF over the valid moves in move order: one coalesced
+// pass for the total, then 32 moves at a time with a warp scan until the
+// running sum passes u * total.
+__global__ void __launch_bounds__(256, 4) lt_propose_kernel(LearnedDev d, MoveTable mt, unsigned t,
                                                          int count_stats,
                                                          unsigned char* prop_slots) {
-  __shared__ unsigned char s_occ[8][2 * kPtMaxN];
-  __shared__ unsigned char s_slot[8][kPtMaxN + 1];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, c = blockIdx.x * 8 + w;
-  if (c >= d.B) return;
-  const int ladder = c / d.M, r = d.rung[c], E = d.E[c];
-  if (lane == 0 && count_stats) d.hist[((size_t)ladder * d.M + r) * d.nb + E] += 1;
-  load_state(d.slots + (size_t)c * d.n, d.n, d.delta, s_slot[w], s_occ[w], lane);
-  const float* z = d.Zcur + (size_t)c * d.NMp;
-  const float lse = d.lse[c];
-  const uint4 rw = philox4x32_10(make_uint4(t, (unsigned)r, (unsigned)ladder, 5u), d.key0, d.key1);
-  // inverse CDF over the valid moves: lane-contiguous chunks, warp scan
-  const int CH = (mt.NM + 31) / 32, m0 = lane * CH, m1 = min(mt.NM, m0 + CH);
-  float part = 0.f;
-  int k = 1;
-  while (m0 < mt.NM && m0 >= mt.off[k + 1]) ++k;
-  const int k0 = k;
-  for (int m = m0; m < m1; ++m) {
-    while (m >= mt.off[k + 1]) ++k;
-    if (m - mt.off[k] != s_slot[w][k]) part += expf(z[m] - lse);
-  }
-  float incl = part;
+  __shared__ MoveMaps mm;
+  __shared__ int s_occ[8][2 * kPtMaxN];
+  __shared__ unsigned char s_slot[8][kPtMaxN + 8];
+  build_move_maps(mt, mm);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c = blockIdx.x * 8 + w; c < d.B; c += gridDim.x * 8) {
+    const int ladder = c / d.M, r = d.rung[c], E = d.E[c];
+    if (lane == 0 && count_stats) d.hist[((size_t)ladder * d.M + r) * d.nb + E] += 1;
+    load_state(d.slots + (size_t)c * d.n, d.n, d.delta, s_slot[w], s_occ[w], lane);
+    const float* z = d.Zcur + (size_t)c * d.NMp;
+    const float lse = d.lse[c];
+    const int NM = mt.NM;
+    const uint4 rw = philox4x32_10(make_uint4(t, (unsigned)r, (unsigned)ladder, 5u), d.key0, d.key1);
+    float part = 0.f;
+    for (int m = lane; m < NM; m += 32)
+      if (valid_move(mm, s_slot[w], m)) part += __expf(z[m] - lse);
+    const float total = warp_sum(part);
+    const float target = ((float)rw.x + 0.5f) * 2.3283064365386963e-10f * total;
+    float run = 0.f;
+    int pick = -1, last = -1;
+    for (int base = 0; base < NM; base += 32) {
+      const int m = base + lane;
+      const bool ok = m < NM && valid_move(mm, s_slot[w], m);
+      const float v = ok ? __expf(z[m] - lse) : 0.f;
+      float incl = v;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const float v = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += v;
-  }
-  const float total = __shfl_sync(0xffffffffu, incl, 31);
-  const float target = ((float)rw.x + 0.5f) * 2.3283064365386963e-10f * total;
-  const unsigned hit = __ballot_sync(0xffffffffu, incl >= target && part > 0.f);
-  const int owner = hit ? __ffs(hit) - 1 : 31;
-  int pick = -1;
-  if (lane == owner) {
-    float cum = incl - part;
-    k = k0;
-    for (int m = m0; m < m1; ++m) {
-      while (m >= mt.off[k + 1]) ++k;
-      if (m - mt.off[k] == s_slot[w][k]) continue;
-      cum += expf(z[m] - lse);
-      pick = m;
-      if (cum >= target) break;
+      for (int o = 1; o < 32; o <<= 1) {
+        const float u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+      }
+      const unsigned valid = __ballot_sync(0xffffffffu, ok);
+      if (valid) last = base + 31 - __clz(valid);
+      const unsigned hit = __ballot_sync(0xffffffffu, ok && run + incl >= target);
+      if (hit) {
+        pick = base + __ffs(hit) - 1;
+        break;
+      }
+      run += __shfl_sync(0xffffffffu, incl, 31);
     }
-  }
-  pick = __shfl_sync(0xffffffffu, pick, owner);
-  if (pick < 0) {                     // rounding left nothing: last valid move
-    int last = -1;
-    for (int m = lane, kk = 1; m < mt.NM; m += 32) {
-      while (m >= mt.off[kk + 1]) ++kk;
-      if (m - mt.off[kk] != s_slot[w][kk]) last = m;
+    if (pick < 0) pick = last < 0 ? 0 : last;   // rounding left the target just above the total
+    const int kp = mm.k[pick];
+    const int s_new = mm.s[pick], s_old = s_slot[w][kp];
+    const int dE = move_delta_e(s_occ[w], s_old, kp + d.delta, s_new);
+    unsigned char* ps = prop_slots + (size_t)c * d.n;
+    for (int i = lane; i < d.n; i += 32)
+      ps[i] = (i + 1 == kp) ? (unsigned char)s_new : s_slot[w][i + 1];
+    if (lane == 0) {
+      d.prop[c] = make_int4(kp, s_old, s_new, dE);
+      d.lq_fwd[c] = z[pick] - lse;
     }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) last = max(last, __shfl_xor_sync(0xffffffffu, last, o));
-    pick = last;
-  }
-  int kp = 1;
-  while (pick >= mt.off[kp + 1]) ++kp;
-  const int s_new = pick - mt.off[kp], s_old = s_slot[w][kp];
-  const int dE = move_delta_e(s_occ[w], s_old, kp + d.delta, s_new);
-  unsigned char* ps = prop_slots + (size_t)c * d.n;
-  for (int i = lane; i < d.n; i += 32)
-    ps[i] = (i + 1 == kp) ? (unsigned char)s_new : s_slot[w][i + 1];
-  if (lane == 0) {
-    d.prop[c] = make_int4(kp, s_old, s_new, dE);
-    d.lq_fwd[c] = z[pick] - lse;
+    __syncwarp();
   }
 }
 
 // Metropolis-Hastings acceptance with the proposed states' logits Zp.
-__global__ void __launch_bounds__(256) lt_accept_kernel(LearnedDev d, MoveTable mt, unsigned t,
+__global__ void __launch_bounds__(256, 4) lt_accept_kernel(LearnedDev d, MoveTable mt, unsigned t,
                                                         const unsigned char* prop_slots,
                                                         const float* Zp) {
-  __shared__ unsigned char s_occ[8][2 * kPtMaxN];
-  __shared__ unsigned char s_slot[8][kPtMaxN + 1];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, c = blockIdx.x * 8 + w;
-  if (c >= d.B) return;
-  const int ladder = c / d.M, r = d.rung[c];
-  load_state(prop_slots + (size_t)c * d.n, d.n, d.delta, s_slot[w], s_occ[w], lane);
-  const float* zp = Zp + (size_t)c * d.NMp;
-  const float lse_p = valid_lse(zp, mt, s_slot[w], lane);
-  const int4 pr = d.prop[c];
-  const float lq_rev = zp[mt.off[pr.x] + pr.y] - lse_p;
-  const float log_a = (float)(-d.beta[r] * (double)pr.w) + lq_rev - d.lq_fwd[c];
-  const uint4 rw = philox4x32_10(make_uint4(t, (unsigned)r, (unsigned)ladder, 5u), d.key0, d.key1);
-  const float u = ((float)rw.y + 0.5f) * 2.3283064365386963e-10f;
-  const bool acc = log_a >= 0.f || logf(u) < log_a;
-  if (!acc) return;
-  for (int i = lane; i < d.n; i += 32) d.slots[(size_t)c * d.n + i] = s_slot[w][i + 1];
-  float* zc = d.Zcur + (size_t)c * d.NMp;
-  for (int m = lane; m < d.NMp; m += 32) zc[m] = zp[m];
-  if (lane == 0) {
-    d.lse[c] = lse_p;
-    d.E[c] += pr.w;
-    d.accm[(size_t)ladder * d.M + r] += 1;
+  __shared__ MoveMaps mm;
+  __shared__ unsigned char s_slot[8][kPtMaxN + 8];
+  build_move_maps(mt, mm);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c = blockIdx.x * 8 + w; c < d.B; c += gridDim.x * 8) {
+    const int ladder = c / d.M, r = d.rung[c];
+    load_state(prop_slots + (size_t)c * d.n, d.n, d.delta, s_slot[w], nullptr, lane);
+    const float* zp = Zp + (size_t)c * d.NMp;
+    const float lse_p = valid_lse(zp, mm, mt.NM, s_slot[w], lane);
+    const int4 pr = d.prop[c];
+    const float lq_rev = zp[mt.off[pr.x] + pr.y] - lse_p;
+    const float log_a = (float)(-d.beta[r] * (double)pr.w) + lq_rev - d.lq_fwd[c];
+    const uint4 rw = philox4x32_10(make_uint4(t, (unsigned)r, (unsigned)ladder, 5u), d.key0, d.key1);
+    const float u = ((float)rw.y + 0.5f) * 2.3283064365386963e-10f;
+    const bool acc = log_a >= 0.f || logf(u) < log_a;
+    if (acc) {
+      for (int i = lane; i < d.n; i += 32) d.slots[(size_t)c * d.n + i] = s_slot[w][i + 1];
+      float* zc = d.Zcur + (size_t)c * d.NMp;
+      for (int m = lane; m < d.NMp; m += 32) zc[m] = zp[m];
+      if (lane == 0) {
+        d.lse[c] = lse_p;
+        d.E[c] += pr.w;
+        d.accm[(size_t)ladder * d.M + r] += 1;
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -265,6 +296,12 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return SK_ECUDA;
     own = true;
   }
+  // the per-chain kernels loop over chains, 8 per block, 8 blocks per SM (two
+  // waves of the 4 resident ones)
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int chain_grid = std::min((B + 7) / 8, 8 * (sms > 0 ? sms : 1));
   LearnedDev d;
   std::memset(&d, 0, sizeof(d));
   d.n = n; d.delta = m->delta; d.M = M; d.L = L; d.B = B; d.nb = nb; d.NMp = m->NMp;
@@ -320,15 +357,15 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
   }
   if (e == cudaSuccess) e = mlp_forward_dev(*m, Bp, s);
   if (e == cudaSuccess) {
-    lt_keep_kernel<<<(B + 7) / 8, 256, 0, s>>>(d, mt, m->Z);
+    lt_keep_kernel<<<chain_grid, 256, 0, s>>>(d, mt, m->Z);
     e = cudaGetLastError();
   }
   for (uint64_t t = 0; t < iters && e == cudaSuccess; ++t) {
-    lt_propose_kernel<<<(B + 7) / 8, 256, 0, s>>>(d, mt, (unsigned)t, t >= burnin ? 1 : 0,
+    lt_propose_kernel<<<chain_grid, 256, 0, s>>>(d, mt, (unsigned)t, t >= burnin ? 1 : 0,
                                                   m->slots);
     e = mlp_forward_dev(*m, Bp, s);
     if (e != cudaSuccess) break;
-    lt_accept_kernel<<<(B + 7) / 8, 256, 0, s>>>(d, mt, (unsigned)t, m->slots, m->Z);
+    lt_accept_kernel<<<chain_grid, 256, 0, s>>>(d, mt, (unsigned)t, m->slots, m->Z);
     lt_exchange_kernel<<<(L + 3) / 4, 128, 0, s>>>(d, (unsigned)t);
     e = cudaGetLastError();
   }
