@@ -517,8 +517,8 @@ __host__ __device__ constexpr DigitPlan permute_plan(int DELTA, int N, DigitPlan
 // grouping of least estimated cost; rule 1 takes the tail form with the last
 // factors below 2^14 as tail and contiguous greedy groups.  The entries were
 // chosen by timing every variant on the GB300 (2^34-term slices of S(n),
-// L(n)); plans of equal cost can differ by 10-30 % in speed because the
-// compiler schedules them differently.
+// L(n), compiled as the library is); plans of equal cost can differ by up to
+// 30 % in speed because the compiler schedules them differently.
 struct PlanVariant {
   int rule, greedy, tree;
   unsigned seed;
@@ -527,11 +527,11 @@ __host__ __device__ constexpr PlanVariant plan_variant(int DELTA, int N) {
   if (N < 14) return {0, 1, 0, 0};
   if (N > 24) return {0, 0, 0, 0};
   constexpr PlanVariant skolem[11] = {
-      {0, 1, 0, 0}, {0, 0, 0, 0}, {0, 1, 0, 0}, {0, 1, 1, 0}, {0, 1, 1, 0}, {1, 0, 1, 4},
-      {0, 0, 1, 2}, {1, 0, 1, 0}, {1, 0, 1, 0}, {0, 0, 1, 0}, {0, 1, 1, 0}};
+      {0, 1, 0, 0}, {0, 0, 0, 0}, {0, 1, 0, 1}, {1, 0, 1, 1}, {1, 0, 0, 2}, {1, 0, 1, 2},
+      {0, 0, 1, 1}, {0, 1, 0, 0}, {1, 0, 1, 1}, {0, 1, 1, 0}, {1, 0, 0, 0}};
   constexpr PlanVariant langford[11] = {
-      {1, 0, 0, 0}, {0, 1, 1, 0}, {1, 0, 0, 0}, {0, 1, 1, 0}, {0, 0, 1, 0}, {0, 0, 1, 1},
-      {0, 0, 1, 1}, {0, 0, 1, 0}, {0, 1, 1, 0}, {0, 0, 0, 0}, {0, 1, 0, 0}};
+      {1, 0, 0, 0}, {0, 1, 1, 0}, {0, 1, 0, 2}, {1, 0, 0, 1}, {1, 0, 0, 0}, {1, 0, 0, 3},
+      {1, 0, 0, 2}, {0, 0, 1, 1}, {1, 0, 0, 0}, {0, 1, 0, 2}, {1, 0, 1, 1}};
   return DELTA ? langford[N - 14] : skolem[N - 14];
 }
 
@@ -734,11 +734,32 @@ __host__ __device__ __forceinline__ unsigned long long horner31_mod(unsigned lon
   return v;
 }
 
+// Residues of (flip ? -1 : 1) * sum_{i<K} a_i 2^{31 i} modulo the primes.
+// Kept out of line: code around the walk changes how the compiler allocates
+// and schedules the walk itself (by up to 10 % in speed), so the item
+// function holds the walk and little else.
+constexpr int kMaxDigits = 6;
+static __device__ __noinline__ void reduce_digits(const long long (&a)[kMaxDigits], int K, bool flip,
+                                           int nprimes, const Primes* P,
+                                           unsigned long long (&res)[kMaxPrimes]) {
+  for (int j = 0; j < kMaxPrimes; ++j) {
+    if (j >= nprimes) {
+      res[j] = 0;
+      continue;
+    }
+    const unsigned long long p = (unsigned long long)P->pr[j].p;
+    unsigned long long u = 0;
+    for (int i = K - 1; i >= 0; --i) u = horner31_mod(u, signed_mod(a[i], p), p);
+    res[j] = (flip && u) ? p - u : u;
+  }
+}
+
 // Accumulator of the exact form: one 64-bit signed word per digit.
 template <int DELTA, int N>
 struct LimbAcc {
   static constexpr int K = make_digit_plan(DELTA, N).kd;
   static constexpr int TAIL = make_digit_plan(DELTA, N).tail_form;
+  static_assert(K <= kMaxDigits, "digits of the exact product");
   const Primes& P;
   long long acc[K];
   __device__ __forceinline__ explicit LimbAcc(const Primes& P_) : P(P_) {
@@ -765,18 +786,10 @@ struct LimbAcc {
   // residues of (flip ? -1 : 1) * sum_i acc_i 2^{31 i}, in [0, p)
   __device__ __forceinline__ void finish(bool flip, int nprimes,
                                          unsigned long long (&res)[kMaxPrimes]) {
+    long long a[kMaxDigits] = {};
 #pragma unroll
-    for (int j = 0; j < kMaxPrimes; ++j) {
-      if (j >= nprimes) {
-        res[j] = 0;
-        continue;
-      }
-      const unsigned long long p = (unsigned long long)P.pr[j].p;
-      unsigned long long u = 0;
-#pragma unroll
-      for (int i = K - 1; i >= 0; --i) u = horner31_mod(u, signed_mod(acc[i], p), p);
-      res[j] = (flip && u) ? p - u : u;
-    }
+    for (int i = 0; i < K; ++i) a[i] = acc[i];
+    reduce_digits(a, K, flip, nprimes, &P, res);
   }
 };
 

@@ -22,7 +22,7 @@ def test_batch_small_all_variants_vs_oracle():
 
 @pytest.mark.parametrize("kw", [{}, {"no_graph": True}, {"mode": sk.BATCH_PER_JOB},
                                 {"block_threads": 128, "repeats": 2},
-                                {"walk_bits": {16: 8, 17: 20}, "nprimes": 4}])
+                                {"walk_bits": {16: 8, 17: 18}, "nprimes": 4}])
 def test_batch_modes_agree(kw, skolem_table, langford_table):
     jobs = [(0, 16), (1, 16), (2, 15), (0, 17), (1, 15), (0, 13), (2, 5), (1, 4), (0, 1)]
     counts, stat, rep = sk.count_batch(jobs, **kw)
