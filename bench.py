@@ -186,6 +186,24 @@ def dist_setup(n_gpus):
     return world, rank, local
 
 
+def reduce_max_over_ranks(values, device):
+    """Maximum over the ranks of each of a few floats (the slowest rank's
+    time); the values unchanged with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def job_throughput(world, steps, units_per_step, seconds):
+    """Units processed by all ranks (one replica of the workload each) per
+    second of the slowest rank."""
+    return world * steps * units_per_step / seconds
+
+
 def source_hash():
     h = hashlib.sha256()
     for f in ("sk_exact.cuh", "sk_exact_launch.cuh"):
@@ -406,15 +424,12 @@ def run_ours(args, world, rank, local):
     clk = clocks.stop()
     dev_s = e0.elapsed_time(e1) / 1e3
     wall_s = w1 - w0
-    if world > 1:
-        t = torch.tensor([dev_s, wall_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dev_s, wall_s = float(t[0]), float(t[1])
+    dev_s, wall_s = reduce_max_over_ranks([dev_s, wall_s], "cuda")
     if rank != 0:
         return
     tps = terms_per_step()
-    value = world * args.steps * tps / dev_s
-    e2e = world * args.steps * tps / wall_s
+    value = job_throughput(world, args.steps, tps, dev_s)
+    e2e = job_throughput(world, args.steps, tps, wall_s)
     # roofline of the dominant kernel: the largest launch (S(20))
     dom = [x for x in per_launch if x[0] == (0, 20)]
     dom_ms = statistics.mean(x[1] for x in dom)
