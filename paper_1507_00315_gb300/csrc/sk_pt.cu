@@ -13,10 +13,88 @@
 
 namespace sk {
 
+// Per-warp view of one ladder's tables and this lane's per-rung constants.
+struct PtLane {
+  unsigned short* hist;                 // [E][32]
+  unsigned char* slot;                  // [k][32], k = 1..n
+  unsigned char* occ;                   // [b][32]
+  unsigned long long tm1, tm2;          // move thresholds at this lane's rung, dE = 1, 2
+  const unsigned long long* tswap;      // [M][bins+1]
+  int lane, M, n, delta, bins, nb;
+  unsigned burnin;
+  bool active;                          // lane < M
+};
+
+// Iteration t at rung `lane`, Philox block wc: the energy statistic, one
+// Metropolis move of the configuration in column c (energy E), then the
+// exchange of this lane's pair (j, j+1), j = t mod 2.  Branch-free: every
+// store and the threshold load happen, with unchanged values where a move
+// or exchange is rejected.
+__device__ __forceinline__ void pt_step(const PtLane& S, const uint4 wc, const unsigned t, int& c,
+                                        int& E, unsigned& accm, unsigned& accs) {
+  const int lane = S.lane;
+  const unsigned xw_lo = __shfl_up_sync(0xffffffffu, wc.w, 1);    // word 3 of rung lane-1
+  S.hist[E * 32 + lane] += (unsigned short)(S.active && t >= S.burnin);
+  // Metropolis move: pair k to another start slot
+  const int k = 1 + (int)__umulhi(wc.x, (unsigned)S.n);
+  const int d = k + S.delta;
+  const int L = S.bins - d;
+  unsigned char* sk = &S.slot[k * 32 + c];
+  const int s_old = *sk;
+  // L = 1 (Langford n = 2, k = 2): no other slot; s_new = s_old keeps the
+  // reads inside the table and the move is never taken
+  int s_new = s_old;
+  if (L >= 2) {
+    s_new = (int)__umulhi(wc.y, (unsigned)(L - 1));
+    s_new += s_new >= s_old;
+  }
+  unsigned char* o1 = &S.occ[s_old * 32 + c];
+  unsigned char* o2 = &S.occ[(s_old + d) * 32 + c];
+  unsigned char* o3 = &S.occ[s_new * 32 + c];
+  unsigned char* o4 = &S.occ[(s_new + d) * 32 + c];
+  const int a1 = *o1, a2 = *o2, a3 = *o3, a4 = *o4;
+  // dE: taking the pair out empties the bins it was alone in; putting it
+  // back fills the empty bins it lands on (a new bin may be the old pair's
+  // other bin: s_new = s_old + d or s_new + d = s_old)
+  const int b3 = a3 - (s_new == s_old + d);
+  const int b4 = a4 - (s_new + d == s_old);
+  const int dE = (a1 == 1) + (a2 == 1) - (b3 == 0) - (b4 == 0);
+  const unsigned long long thr = dE <= 0 ? (1ull << 32) : (dE == 1 ? S.tm1 : S.tm2);
+  const bool acc = S.active && L >= 2 && (unsigned long long)wc.z < thr;
+  // counts written in this order are right when bins coincide: o3 == o2
+  // ends at b3 + 1 = a2, o4 == o1 at b4 + 1 = a1
+  const int ai = acc;
+  *o1 = (unsigned char)(a1 - ai);
+  *o2 = (unsigned char)(a2 - ai);
+  *o3 = (unsigned char)(acc ? b3 + 1 : a3);
+  *o4 = (unsigned char)(acc ? b4 + 1 : a4);
+  *sk = (unsigned char)(acc ? s_new : s_old);
+  E += acc ? dE : 0;
+  accm += ai;
+  __syncwarp();
+  // exchange: both lanes of a pair take the same decision from the lower
+  // rung's word 3
+  const int pk = (E << 8) | c;
+  const int dn = __shfl_down_sync(0xffffffffu, pk, 1);
+  const int up = __shfl_up_sync(0xffffffffu, pk, 1);
+  const int par = (lane ^ (int)t) & 1;                // 0: lower lane of its pair, 1: upper
+  const int row = lane - par;                         // the pair (row, row + 1)
+  const bool valid = row >= 0 && row + 1 < S.M;
+  const int o = par ? up : dn;
+  const int de = par ? (o >> 8) - E : E - (o >> 8);
+  const unsigned xw = par ? xw_lo : wc.w;
+  const unsigned long long T = __ldg(S.tswap + (valid ? row : 0) * S.nb + (de > 0 ? de : 0));
+  const bool dec = valid && (de <= 0 || (unsigned long long)xw < T);
+  c = dec ? (o & 0xff) : c;
+  E = dec ? (o >> 8) : E;
+  accs += dec && !par;
+}
+
 // One warp = one ladder; persistent over ladders.  Per iteration t, in the
 // order of Algorithm 2: the energy statistics of every rung (after burn-in),
 // one Metropolis move per configuration, then the exchanges of the pairs
-// (j, j+1) with j = t mod 2.
+// (j, j+1) with j = t mod 2.  Lane j serves rung j (see sk_pt.cuh): it holds
+// the column c of the configuration now at rung j and its energy E.
 __global__ void __launch_bounds__(128, 7)
     pt_kernel(PtParams p, const unsigned long long* __restrict__ tmove_g,
               const unsigned long long* __restrict__ tswap_g, unsigned long long* hist_g,
@@ -24,28 +102,39 @@ __global__ void __launch_bounds__(128, 7)
   extern __shared__ __align__(16) unsigned char pt_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int M = p.M, n = p.n, bins = p.bins, nb = bins + 1;
-  const unsigned long long* tmove = tmove_g;                           // [M][3]
-  const unsigned long long* tswap = tswap_g;                           // [M][bins+1]
-  unsigned char* wbase = pt_smem + (size_t)warp * pt_warp_bytes(M, n);
-  unsigned short* hist = (unsigned short*)wbase;                       // [M][bins+1]
-  unsigned* accm = (unsigned*)(wbase + ((size_t)M * nb * 2 + 15) / 16 * 16);   // [M]
-  unsigned* accs = accm + M;                                           // [M]
-  unsigned char* slot = (unsigned char*)(accs + M);                    // [k][32], k = 1..n
-  unsigned char* occ = slot + (n + 1) * 32;                            // [b][32]
-  const bool active = lane < M;
+  unsigned char* wbase = pt_smem + (size_t)warp * pt_warp_bytes(n);
+  PtLane S;
+  S.hist = (unsigned short*)wbase;
+  S.slot = wbase + ((size_t)nb * 64 + 15) / 16 * 16;
+  S.occ = S.slot + (n + 1) * 32;
+  S.lane = lane;
+  S.M = M;
+  S.n = n;
+  S.delta = p.delta;
+  S.bins = bins;
+  S.nb = nb;
+  S.burnin = p.burnin;
+  S.active = lane < M;
+  S.tm1 = S.active ? __ldg(&tmove_g[lane * 2]) : 0ull;
+  S.tm2 = S.active ? __ldg(&tmove_g[lane * 2 + 1]) : 0ull;
+  S.tswap = tswap_g;
+  unsigned short* hist = S.hist;
+  unsigned char* slot = S.slot;
+  unsigned char* occ = S.occ;
+  const bool active = S.active;
   for (int ladder = blockIdx.x * p.warps_per_block + warp; ladder < p.ladders;
        ladder += gridDim.x * p.warps_per_block) {
-    for (int i = lane; i < M * nb; i += 32) hist[i] = 0;
-    for (int i = lane; i < M; i += 32) { accm[i] = 0; accs[i] = 0; }
+    for (int e = 0; e < nb; ++e) hist[e * 32 + lane] = 0;
     for (int b = 0; b < bins; ++b) occ[b * 32 + lane] = 0;
-    int r = lane;           // rung (temperature) of this lane's configuration
-    int lor = lane;         // lane holding rung `lane`
-    int E = 0;
+    for (int k = 0; k <= n; ++k) slot[k * 32 + lane] = 0;
+    // column `lane` <- the configuration that starts at rung `lane`
+    int c = lane, E = 0;
+    unsigned accm = 0, accs = 0;
     if (active) {
       for (int k = 1; k <= n; ++k) {
         const unsigned L = (unsigned)(bins - (k + p.delta));
-        const uint4 w = philox4x32_10(make_uint4((unsigned)k, (unsigned)r, (unsigned)ladder, 1u),
-                                      p.key0, p.key1);
+        const uint4 w = philox4x32_10_rk(
+            make_uint4((unsigned)k, (unsigned)lane, (unsigned)ladder, 1u), p.rk);
         const int s = (int)__umulhi(w.x, L);
         slot[k * 32 + lane] = (unsigned char)s;
         occ[s * 32 + lane] += 1;
@@ -54,80 +143,37 @@ __global__ void __launch_bounds__(128, 7)
       for (int b = 0; b < bins; ++b) E += occ[b * 32 + lane] == 0;
     }
     __syncwarp();
-    for (unsigned long long t = 0; t < p.iters; ++t) {
-      const unsigned tt = (unsigned)t;
-      if ((tt & (kPtFlush - 1)) == 0 && t > 0) {       // 16-bit counters: flush
-        __syncwarp();
-        for (int i = lane; i < M * nb; i += 32)
-          if (hist[i]) { atomicAdd(&hist_g[i], (unsigned long long)hist[i]); hist[i] = 0; }
-        __syncwarp();
+    for (unsigned long long t0 = 0; t0 < p.iters; t0 += kPtFlush) {
+      const unsigned t1 = (unsigned)(t0 + kPtFlush < p.iters ? t0 + kPtFlush : p.iters);
+      // two iterations a trip, each one's Philox block computed while the
+      // other waits on shared memory (the blocks do not depend on the state)
+      uint4 wa = philox4x32_10_rk(make_uint4((unsigned)t0, (unsigned)lane, (unsigned)ladder, 2u), p.rk);
+      unsigned t = (unsigned)t0;
+      for (; t + 1 < t1; t += 2) {
+        const uint4 wb = philox4x32_10_rk(make_uint4(t + 1u, (unsigned)lane, (unsigned)ladder, 2u), p.rk);
+        pt_step(S, wa, t, c, E, accm, accs);
+        wa = philox4x32_10_rk(make_uint4(t + 2u, (unsigned)lane, (unsigned)ladder, 2u), p.rk);
+        pt_step(S, wb, t + 1, c, E, accm, accs);
       }
-      unsigned xw = 0;                                 // word 3 of this lane's move block
-      if (active) {
-        if (t >= p.burnin) hist[r * nb + E] += 1;
-        const uint4 w = philox4x32_10(make_uint4(tt, (unsigned)r, (unsigned)ladder, 2u), p.key0,
-                                      p.key1);
-        xw = w.w;
-        const int k = 1 + (int)__umulhi(w.x, (unsigned)n);
-        const int d = k + p.delta;
-        const int L = bins - d;
-        if (L >= 2) {
-          const int s_old = slot[k * 32 + lane];
-          int s_new = (int)__umulhi(w.y, (unsigned)(L - 1));
-          if (s_new >= s_old) ++s_new;
-          // dE from the four occupancies read at once: taking the pair out
-          // empties the bins it was alone in; putting it back fills the
-          // empty bins it lands on (s_new != s_old; a new bin may be the old
-          // pair's other bin)
-          unsigned char* o1 = &occ[s_old * 32 + lane];
-          unsigned char* o2 = &occ[(s_old + d) * 32 + lane];
-          unsigned char* o3 = &occ[s_new * 32 + lane];
-          unsigned char* o4 = &occ[(s_new + d) * 32 + lane];
-          const int a1 = *o1, a2 = *o2, a3 = *o3, a4 = *o4;
-          const int b3 = a3 - (s_new == s_old + d);
-          const int b4 = a4 - (s_new + d == s_old);
-          const int dE = (a1 == 1) + (a2 == 1) - (b3 == 0) - (b4 == 0);
-          if (dE <= 0 || (unsigned long long)w.z < __ldg(&tmove[r * 3 + dE])) {
-            --(*o1);                                 // one after the other: bins may coincide
-            --(*o2);
-            ++(*o3);
-            ++(*o4);
-            E += dE;
-            slot[k * 32 + lane] = (unsigned char)s_new;
-            accm[r] += 1;
-          }
+      if (t < t1) pt_step(S, wa, t, c, E, accm, accs);
+      if (t1 < p.iters && active)                  // 16-bit counters: flush this rung's column
+        for (int e = 0; e < nb; ++e) {
+          const unsigned v = hist[e * 32 + lane];
+          if (v) { atomicAdd(&hist_g[(size_t)lane * nb + e], (unsigned long long)v); hist[e * 32 + lane] = 0; }
         }
-      }
-      // exchanges: lane j acts for rung j
-      const int Er = __shfl_sync(0xffffffffu, E, lor);
-      const unsigned xr = __shfl_sync(0xffffffffu, xw, lor);   // word 3 of rung `lane`'s block
-      const int En = __shfl_down_sync(0xffffffffu, Er, 1);
-      int dec = 0;
-      if (lane + 1 < M && (lane & 1) == (int)(tt & 1u)) {
-        const int de = Er - En;
-        dec = (de <= 0 || (unsigned long long)xr < __ldg(&tswap[lane * nb + de])) ? 1 : 0;
-        if (dec) accs[lane] += 1;
-      }
-      const int lor_down = __shfl_down_sync(0xffffffffu, lor, 1);
-      const int lor_up = __shfl_up_sync(0xffffffffu, lor, 1);
-      const int dec_up = __shfl_up_sync(0xffffffffu, dec, 1);
-      lor = dec ? lor_down : ((lane > 0 && dec_up) ? lor_up : lor);
-      const int d_r = __shfl_sync(0xffffffffu, dec, r & 31);
-      const int d_rm = __shfl_sync(0xffffffffu, dec, (r + 31) & 31);
-      if (active) r = d_r ? r + 1 : ((r > 0 && d_rm) ? r - 1 : r);
-      __syncwarp();
     }
     // flush this ladder
-    __syncwarp();
-    for (int i = lane; i < M * nb; i += 32)
-      if (hist[i]) atomicAdd(&hist_g[i], (unsigned long long)hist[i]);
-    for (int i = lane; i < M; i += 32) {
-      if (accm[i]) atomicAdd(&accm_g[i], (unsigned long long)accm[i]);
-      if (accs[i]) atomicAdd(&accs_g[i], (unsigned long long)accs[i]);
+    if (active) {
+      for (int e = 0; e < nb; ++e) {
+        const unsigned v = hist[e * 32 + lane];
+        if (v) atomicAdd(&hist_g[(size_t)lane * nb + e], (unsigned long long)v);
+      }
+      if (accm) atomicAdd(&accm_g[lane], (unsigned long long)accm);
+      if (accs) atomicAdd(&accs_g[lane], (unsigned long long)accs);
+      if (final_slots)
+        for (int k = 1; k <= n; ++k)
+          final_slots[((size_t)ladder * M + lane) * n + (k - 1)] = slot[k * 32 + c];
     }
-    if (final_slots && active)
-      for (int k = 1; k <= n; ++k)
-        final_slots[((size_t)ladder * M + r) * n + (k - 1)] = slot[k * 32 + lane];
     __syncwarp();
   }
 }
@@ -173,9 +219,10 @@ int pt_run_impl(int variant, int n, int M, const double* beta, int L, uint64_t i
   st = check_device();
   if (st) return st;
   const int bins = 2 * n, nb = bins + 1;
-  std::vector<unsigned long long> tm((size_t)M * 3, 0), ts((size_t)M * nb, 0);
+  // thresholds: moves [M][dE = 1, 2], exchanges [M][de]
+  std::vector<unsigned long long> tm((size_t)M * 2, 0), ts((size_t)M * nb, 0);
   for (int j = 0; j < M; ++j) {
-    for (int de = 1; de <= 2; ++de) tm[j * 3 + de] = accept_threshold(beta[j] * (double)de);
+    for (int de = 1; de <= 2; ++de) tm[j * 2 + de - 1] = accept_threshold(beta[j] * (double)de);
     if (j + 1 < M)
       for (int de = 1; de <= bins; ++de)
         ts[j * nb + de] = accept_threshold((beta[j + 1] - beta[j]) * (double)de);
@@ -187,11 +234,14 @@ int pt_run_impl(int variant, int n, int M, const double* beta, int L, uint64_t i
   p.bins = bins;
   p.ladders = L;
   p.warps_per_block = 4;
-  p.iters = iters;
-  p.burnin = burnin;
+  p.iters = (unsigned)iters;
+  p.burnin = (unsigned)std::min<uint64_t>(burnin, iters);
   p.key0 = (unsigned)seed;
   p.key1 = (unsigned)(seed >> 32);
-  const size_t smem = pt_smem_bytes(M, n, p.warps_per_block);
+  for (int r = 0; r < 10; ++r) {
+    p.rk[2 * r] = p.key0 + 0x9E3779B9u * (unsigned)r;
+    p.rk[2 * r + 1] = p.key1 + 0xBB67AE85u * (unsigned)r;
+  }
   const size_t n_hist = (size_t)M * nb, n_fin = final_slots ? (size_t)L * M * n : 0;
   const size_t bytes = (tm.size() + ts.size() + n_hist + 2 * (size_t)M) * 8 + n_fin;
   cudaStream_t s = (cudaStream_t)stream;
@@ -216,7 +266,9 @@ int pt_run_impl(int variant, int n, int M, const double* beta, int L, uint64_t i
   e = cudaMemcpyAsync(dtm, tm.data(), tm.size() * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dts, ts.data(), ts.size() * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(dh, 0, (n_hist + 2 * (size_t)M) * 8, s);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(pt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = pt_smem_bytes(n, p.warps_per_block);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(pt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -3,11 +3,13 @@
 //
 // State space: the simplified problem of Sec. 3 -- pair k sits at any start
 // bin s in [0, 2n - d_k) of 2n bins, overlaps allowed; the energy is the
-// number of empty bins.  One warp runs one ladder of M <= 32 temperatures;
-// lane l keeps the configuration that started at rung l (its start slots and
-// bin occupancies in shared memory, its energy in a register) and carries a
-// temperature label r that exchanges swap: configurations never move between
-// lanes, labels do (a lane-of-rung table, one entry per lane, follows them).
+// number of empty bins.  One warp runs one ladder of M <= 32 temperatures.
+// Lane j always serves rung j; the configurations stay where they started
+// (column l of the warp's start-slot and bin-occupancy tables in shared
+// memory belongs to the configuration that started at rung l) and an
+// exchange of rungs j, j+1 swaps the column indices and energies that lanes
+// j and j+1 hold.  Per-rung quantities (thresholds, acceptance counters,
+// the energy histogram column) therefore stay with one lane.
 //
 // Random numbers: Philox-4x32-10 (Salmon et al., SC'11), one call per
 // (counter, key): counter (k, rung, ladder, 1) for the start slot of pair k,
@@ -17,7 +19,8 @@
 // 64-bit seed.  (One block per rung and iteration: the exchange needs no
 // call of its own.)
 // Acceptance compares a 32-bit word w with a threshold T = ceil(p 2^32)
-// (T = 2^32: always), i.e. accept iff w / 2^32 < p.
+// (T = 2^32: always; T = 0 where e^-x underflows: never), i.e. accept iff
+// w / 2^32 < p.
 #pragma once
 #include <cstdint>
 
@@ -30,8 +33,9 @@ struct PtParams {
   int n, delta, M, bins;          // bins = 2n
   int ladders;                    // L
   int warps_per_block;
-  unsigned long long iters, burnin;
+  unsigned iters, burnin;
   unsigned key0, key1;
+  unsigned rk[20];                // Philox round keys: (key0 + r W0, key1 + r W1), r = 0..9
 };
 
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1) {
@@ -46,19 +50,32 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1
   return c;
 }
 
-// Shared-memory layout of one warp: the energy histogram (M x (bins+1)
-// 16-bit counters, flushed to global memory every kPtFlush iterations),
-// accepted moves and exchanges (M u32 each), start slots ([k][lane] bytes)
-// and bin occupancies ([b][lane] bytes).  The acceptance thresholds stay in
-// global memory (L1-cached), so about 28 warps fit on an SM.
+// Philox-4x32-10 with the ten round keys given (rk[2r], rk[2r+1] = the key
+// after r bumps): the same function as philox4x32_10, the key schedule
+// computed once on the host.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const unsigned* rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
+  }
+  return c;
+}
+
+// Shared-memory layout of one warp: the energy histogram ([E][rung] 16-bit
+// counters, flushed to global memory every kPtFlush iterations), then the
+// start slots ([k][column]) and bin occupancies ([b][column]), one byte an
+// entry.  Thresholds stay in registers (moves) and global memory, L1-cached
+// (exchanges).
 constexpr unsigned kPtFlush = 32768;
-__host__ __device__ inline size_t pt_warp_bytes(int M, int n) {
-  const size_t hist = ((size_t)M * (2 * n + 1) * 2 + 15) / 16 * 16 + 2 * (size_t)M * 4;
+__host__ __device__ inline size_t pt_warp_bytes(int n) {
+  const size_t hist = ((size_t)(2 * n + 1) * 32 * 2 + 15) / 16 * 16;
   const size_t st = (size_t)(n + 1) * 32 + (size_t)(2 * n) * 32;
   return (hist + st + 15) / 16 * 16;
 }
-__host__ __device__ inline size_t pt_smem_bytes(int M, int n, int wpb) {
-  return (size_t)wpb * pt_warp_bytes(M, n);
+__host__ __device__ inline size_t pt_smem_bytes(int n, int wpb) {
+  return (size_t)wpb * pt_warp_bytes(n);
 }
 
 // Host helpers shared by the plain and the learned chains (sk_pt.cu).

@@ -24,6 +24,8 @@ TABLE6_BETA = [float(r[1]) for r in read_golden("table6_pt_s12.txt")]
     (0, 2, 1, 1, 100, 10, 1),              # smallest: one rung, n = 2
     (1, 3, 32, 1, 400, 40, 9),             # 32 rungs, Langford n = 3
     (0, 33, 32, 1, 300, 30, 3),            # largest order of the workloads
+    (1, 2, 3, 2, 500, 0, 8),               # Langford n = 2: pair 2 has one slot
+    (0, 6, 7, 3, 70000, 35000, 4),         # odd ladder; histogram flushes mid-run
 ])
 def test_trajectory_equals_oracle(variant, n, M, L, iters, burnin, seed):
     beta = TABLE6_BETA if M == 12 else list(np.linspace(0.0, 8.0, M) ** 1.3)
