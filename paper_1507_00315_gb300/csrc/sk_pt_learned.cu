@@ -85,6 +85,15 @@ __device__ __forceinline__ bool valid_move(const MoveMaps& mm, const unsigned ch
   return mm.s[m] != s_slot[mm.k[m]];
 }
 
+// Pull `bytes` bytes at p into L2 (one 128-byte line a lane at a time): a
+// warp asks for the next chain's rows before it works on the current one,
+// so the per-chain loads wait on L2 rather than on HBM.
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes, int lane) {
+  const char* c = (const char*)p;
+  for (size_t o = (size_t)lane * 128; o < bytes; o += 32 * 128)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(c + o));
+}
+
 // log sum exp of the logits z over the valid moves of the state in s_slot:
 // a coalesced pass for the maximum, a second (from L1) for the sum.
 __device__ float valid_lse(const float* z, const MoveMaps& mm, int NM,
@@ -154,6 +163,11 @@ __global__ void __launch_bounds__(256, 4) lt_propose_kernel(LearnedDev d, MoveTa
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int c = blockIdx.x * 8 + w; c < d.B; c += gridDim.x * 8) {
+    const int cn = c + gridDim.x * 8;
+    if (cn < d.B) {
+      prefetch_l2(d.Zcur + (size_t)cn * d.NMp, (size_t)mt.NM * 4, lane);
+      prefetch_l2(d.slots + (size_t)cn * d.n, (size_t)d.n, lane);
+    }
     const int ladder = c / d.M, r = d.rung[c], E = d.E[c];
     if (lane == 0 && count_stats) d.hist[((size_t)ladder * d.M + r) * d.nb + E] += 1;
     load_state(d.slots + (size_t)c * d.n, d.n, d.delta, s_slot[w], s_occ[w], lane);
@@ -212,6 +226,11 @@ __global__ void __launch_bounds__(256, 4) lt_accept_kernel(LearnedDev d, MoveTab
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int c = blockIdx.x * 8 + w; c < d.B; c += gridDim.x * 8) {
+    const int cn = c + gridDim.x * 8;
+    if (cn < d.B) {
+      prefetch_l2(Zp + (size_t)cn * d.NMp, (size_t)mt.NM * 4, lane);
+      prefetch_l2(prop_slots + (size_t)cn * d.n, (size_t)d.n, lane);
+    }
     const int ladder = c / d.M, r = d.rung[c];
     load_state(prop_slots + (size_t)c * d.n, d.n, d.delta, s_slot[w], nullptr, lane);
     const float* zp = Zp + (size_t)c * d.NMp;
