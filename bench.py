@@ -239,7 +239,9 @@ def recorded_imad_busy():
 def run_extra(args, world, rank, local):
     """Extra workloads, one JSON line each: --config batch (all three
     problems, n = 4..nmax, one persistent graph-captured launch vs one launch
-    per job) and --config large (S(24), L(24), four moduli, checkpointed)."""
+    per job), --config large (S(24), L(24), four moduli, checkpointed),
+    --config pt (tempering error vs GPU time, plain and learned proposal) and
+    --config pt-large (tempering at the orders of Tables 7 / 8 above 24)."""
     import torch
     import paper_1507_00315_gb300 as sk
     torch.cuda.set_device(local)
@@ -265,6 +267,8 @@ def run_extra(args, world, rank, local):
                 out["persistent_graph"]["kernel_ms_min"]}
     elif args.config == "pt":
         line = run_pt_bench(args, sk, sh)
+    elif args.config == "pt-large":
+        line = run_pt_large_bench(args, sk, sh)
     else:
         import tempfile
         res = {}
@@ -296,8 +300,14 @@ def run_extra(args, world, rank, local):
 # rungs per iteration (energy difference, threshold test, label update: 2).
 PT_OPS_PER_LANE_ITERATION = 80 + 18 + 3 + 2
 
-EXACT_S = {16: 700078384, 20: 5717789399488, 24: 102388058845620672}
-EXACT_L = {16: 326721800, 20: 2636337861200, 24: 46845158056515936}
+EXACT_S = {16: 700078384, 20: 5717789399488, 24: 102388058845620672,
+           25: 1317281759888482688, 28: 3532373626038214732032,
+           29: 52717585747603598276736}                        # Table 7, exact column
+EXACT_L = {16: 326721800, 20: 2636337861200, 24: 46845158056515936,
+           27: 111683611098764903232, 28: 1607383260609382393152}  # Table 8, exact column
+# the paper's own tempering estimates (Tables 7 / 8, approximate column)
+PAPER_PT_S = {25: 1.317e18, 28: 3.523e21, 29: 5.294e22, 32: 2.213e26, 33: 3.614e27}
+PAPER_PT_L = {27: 1.115e20, 28: 1.603e21, 31: 5.381e24, 32: 8.812e25}
 
 
 def run_pt_bench(args, sk, sh):
@@ -355,6 +365,30 @@ def run_pt_bench(args, sk, sh):
             "config": {"workload": "32 temperatures x 4096 ladders, Skolem / Langford n=16..24",
                        "training": f"{args.pt_samples} plain-PT states, 1 epoch, Adam 1e-3"},
             "unit": "relative error", "results": out}
+
+
+def run_pt_large_bench(args, sk, sh):
+    """Plain tempering beyond the exact workloads: the orders of Tables 7 / 8
+    above 24, errors against the exact counts where the paper has them and
+    the estimate beside the paper's own tempering estimate."""
+    cases = [(0, 25), (0, 28), (0, 29), (1, 27), (1, 28), (0, 32), (0, 33), (1, 31), (1, 32)]
+    out = {}
+    for v, n in cases[:args.pt_cases]:
+        exact = (EXACT_S if v == 0 else EXACT_L).get(n)
+        paper = (PAPER_PT_S if v == 0 else PAPER_PT_L)[n]
+        rows = []
+        for budget in args.pt_budgets:
+            est, rep = sk.pt_estimate(v, n, budget, ladders=4096, seed=budget, stream=sh)
+            rows.append({"iterations": budget, "estimate": est,
+                         "rel_error": (est / exact - 1) if exact else None,
+                         "paper_estimate": paper,
+                         "paper_rel_error": (paper / exact - 1) if exact else None,
+                         "vs_paper_estimate": est / paper - 1, "gpu_ms": rep["kernel_ms"]})
+        out[f"{'SL'[v]}({n})"] = rows
+    return {"metric": "PT estimates beyond n = 24 (Tables 7 / 8)", "unit": "relative error",
+            "config": {"workload": "32 temperatures x 4096 ladders, Skolem n=25..33, "
+                                   "Langford n=27..32"},
+            "results": out}
 
 
 def run_reference(args, world, rank):
@@ -477,9 +511,9 @@ def main():
     ap.add_argument("--pt-budgets", type=int, nargs="+", default=[2000, 8000, 32000])
     ap.add_argument("--pt-learned-budgets", type=int, nargs="+", default=[200, 800])
     ap.add_argument("--pt-samples", type=int, default=10_000_000)
-    ap.add_argument("--pt-cases", type=int, default=6)
-    ap.add_argument("--config", default="mid", choices=["mid", "batch", "large", "pt"],
-                    help="mid: the headline workload; batch / large: extra measurements")
+    ap.add_argument("--pt-cases", type=int, default=9, help="first cases of --config pt / pt-large")
+    ap.add_argument("--config", default="mid", choices=["mid", "batch", "large", "pt", "pt-large"],
+                    help="mid: the headline workload; the others: extra measurements")
     ap.add_argument("--nmax", type=int, default=22, help="largest n of --config batch")
     ap.add_argument("--ckpt-dir", default=None, help="checkpoint directory of --config large")
     args = ap.parse_args()
