@@ -323,8 +323,8 @@ def run_pt_bench(args, sk, sh):
         for budget in sorted(set(args.pt_budgets) | set(args.pt_learned_budgets)):
             est, rep = sk.pt_estimate(v, n, budget, ladders=4096, seed=budget, stream=sh)
             rows.append({"proposal": "plain", "iterations": budget, "estimate": est,
-                         "rel_error": est / exact - 1, "gpu_ms": rep["kernel_ms"],
-                         "tune_ms": rep["tune_ms"]})
+                         "rel_error": est / exact - 1, "rel_stderr": rep["rel_stderr"],
+                         "gpu_ms": rep["kernel_ms"], "tune_ms": rep["tune_ms"]})
         # training set: final states of independent plain runs on the tuned ladder
         beta = sk.tune_ladder(v, n, 32, 32.0, 0)
         states, seed = [], 100
@@ -383,7 +383,8 @@ def run_pt_large_bench(args, sk, sh):
                          "rel_error": (est / exact - 1) if exact else None,
                          "paper_estimate": paper,
                          "paper_rel_error": (paper / exact - 1) if exact else None,
-                         "vs_paper_estimate": est / paper - 1, "gpu_ms": rep["kernel_ms"]})
+                         "vs_paper_estimate": est / paper - 1, "rel_stderr": rep["rel_stderr"],
+                         "gpu_ms": rep["kernel_ms"]})
         out[f"{'SL'[v]}({n})"] = rows
     return {"metric": "PT estimates beyond n = 24 (Tables 7 / 8)", "unit": "relative error",
             "config": {"workload": "32 temperatures x 4096 ladders, Skolem n=25..33, "

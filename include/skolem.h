@@ -241,6 +241,12 @@ typedef struct sk_pt_report {
   double acc_swap[SK_PT_MAX_RUNGS];  /* accepted exchanges of (j, j+1) (W2) */
   double estimate;
   double kernel_ms, tune_ms, wall_ms;
+  /* Relative standard error of `estimate` from the spread of the estimates
+   * of min(16, ladders) equal groups of consecutive ladders (sample standard deviation of the group
+   * estimates / their mean / sqrt(groups)); statistical only, it does not see a ladder
+   * that has not equilibrated.  0 with fewer than 2 groups (ladders < 2) and
+   * for the learned proposal; NaN when the group estimates average to 0. */
+  double rel_stderr;
 } sk_pt_report;
 
 /* Approximate count by parallel tempering (Sec. 3, Algorithm 2): budget =

@@ -141,7 +141,8 @@ class PtReport(ctypes.Structure):
                 ("acc_move", ctypes.c_double * PT_MAX_RUNGS),
                 ("acc_swap", ctypes.c_double * PT_MAX_RUNGS),
                 ("estimate", ctypes.c_double), ("kernel_ms", ctypes.c_double),
-                ("tune_ms", ctypes.c_double), ("wall_ms", ctypes.c_double)]
+                ("tune_ms", ctypes.c_double), ("wall_ms", ctypes.c_double),
+                ("rel_stderr", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         M = self.rungs
@@ -149,7 +150,7 @@ class PtReport(ctypes.Structure):
                 "burnin": self.burnin, "beta": list(self.beta[:M]), "ratio": list(self.ratio[:M]),
                 "acc_move": list(self.acc_move[:M]), "acc_swap": list(self.acc_swap[:M]),
                 "estimate": self.estimate, "kernel_ms": self.kernel_ms,
-                "tune_ms": self.tune_ms, "wall_ms": self.wall_ms}
+                "tune_ms": self.tune_ms, "wall_ms": self.wall_ms, "rel_stderr": self.rel_stderr}
 
 _lib = None
 

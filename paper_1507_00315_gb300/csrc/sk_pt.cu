@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <vector>
 
 #include "sk_host_common.h"
@@ -156,17 +157,21 @@ __global__ void __launch_bounds__(128, 7)
         pt_step(S, wb, t + 1, c, E, accm, accs);
       }
       if (t < t1) pt_step(S, wa, t, c, E, accm, accs);
-      if (t1 < p.iters && active)                  // 16-bit counters: flush this rung's column
+      if (t1 < p.iters && active) {                // 16-bit counters: flush this rung's column
+        unsigned long long* hist_l =
+            hist_g + (size_t)pt_group(ladder, p.ladders, p.groups) * M * nb;
         for (int e = 0; e < nb; ++e) {
           const unsigned v = hist[e * 32 + lane];
-          if (v) { atomicAdd(&hist_g[(size_t)lane * nb + e], (unsigned long long)v); hist[e * 32 + lane] = 0; }
+          if (v) { atomicAdd(&hist_l[(size_t)lane * nb + e], (unsigned long long)v); hist[e * 32 + lane] = 0; }
         }
+      }
     }
     // flush this ladder
     if (active) {
+      unsigned long long* hist_l = hist_g + (size_t)pt_group(ladder, p.ladders, p.groups) * M * nb;
       for (int e = 0; e < nb; ++e) {
         const unsigned v = hist[e * 32 + lane];
-        if (v) atomicAdd(&hist_g[(size_t)lane * nb + e], (unsigned long long)v);
+        if (v) atomicAdd(&hist_l[(size_t)lane * nb + e], (unsigned long long)v);
       }
       if (accm) atomicAdd(&accm_g[lane], (unsigned long long)accm);
       if (accs) atomicAdd(&accs_g[lane], (unsigned long long)accs);
@@ -210,12 +215,16 @@ int pt_check(int variant, int n, int M, const double* beta, int L) {
 }  // namespace
 
 // Runs L ladders for `iters` iterations; host outputs as in the header.
+// With groups > 1 the histograms are also kept per group of ladders
+// (group_hist: groups x M x (2n+1), host), hist being their sum.
 int pt_run_impl(int variant, int n, int M, const double* beta, int L, uint64_t iters,
                 uint64_t burnin, uint64_t seed, uint64_t* hist, uint64_t* accm, uint64_t* accs,
-                uint8_t* final_slots, void* stream, double* kernel_ms) {
+                uint8_t* final_slots, void* stream, double* kernel_ms, int groups = 1,
+                uint64_t* group_hist = nullptr) {
   int st = pt_check(variant, n, M, beta, L);
   if (st) return st;
-  if (!hist || iters > 0xffffffffULL) return SK_EINVAL;
+  if (!hist || iters > 0xffffffffULL || groups < 1 || groups > L || (groups > 1 && !group_hist))
+    return SK_EINVAL;
   st = check_device();
   if (st) return st;
   const int bins = 2 * n, nb = bins + 1;
@@ -242,7 +251,8 @@ int pt_run_impl(int variant, int n, int M, const double* beta, int L, uint64_t i
     p.rk[2 * r] = p.key0 + 0x9E3779B9u * (unsigned)r;
     p.rk[2 * r + 1] = p.key1 + 0xBB67AE85u * (unsigned)r;
   }
-  const size_t n_hist = (size_t)M * nb, n_fin = final_slots ? (size_t)L * M * n : 0;
+  p.groups = groups;
+  const size_t n_hist = (size_t)groups * M * nb, n_fin = final_slots ? (size_t)L * M * n : 0;
   const size_t bytes = (tm.size() + ts.size() + n_hist + 2 * (size_t)M) * 8 + n_fin;
   cudaStream_t s = (cudaStream_t)stream;
   bool own = false;
@@ -297,7 +307,14 @@ int pt_run_impl(int variant, int n, int M, const double* beta, int L, uint64_t i
   cudaFree(d);
   if (own) cudaStreamDestroy(s);
   if (e != cudaSuccess) return cuda_status(e);
-  for (size_t i = 0; i < n_hist; ++i) hist[i] = hh[i];
+  const size_t per = (size_t)M * nb;
+  for (size_t i = 0; i < per; ++i) {
+    unsigned long long v = 0;
+    for (int g = 0; g < groups; ++g) v += hh[(size_t)g * per + i];
+    hist[i] = v;
+  }
+  if (groups > 1)
+    for (size_t i = 0; i < n_hist; ++i) group_hist[i] = hh[i];
   for (int j = 0; j < M; ++j) {
     if (accm) accm[j] = hh[n_hist + j];
     if (accs) accs[j] = hh[n_hist + M + j];
@@ -412,6 +429,9 @@ int pt_estimate_impl(int variant, int n, uint64_t budget, const sk_pt_opts* o, d
   auto t1 = std::chrono::steady_clock::now();
   const int nb = 2 * n + 1;
   std::vector<uint64_t> hist((size_t)M * nb), am(M), as(M);
+  // plain chains: histograms per group of ladders for the standard error
+  const int groups = proposal == SK_PT_LEARNED ? 1 : std::min(kPtErrorGroups, L);
+  std::vector<uint64_t> ghist(groups > 1 ? (size_t)groups * M * nb : 0);
   double kms = 0.0;
   int st;
   if (proposal == SK_PT_LEARNED)
@@ -419,11 +439,25 @@ int pt_estimate_impl(int variant, int n, uint64_t budget, const sk_pt_opts* o, d
                         am.data(), as.data(), o ? o->stream : nullptr, &kms);
   else
     st = pt_run_impl(variant, n, M, beta.data(), L, budget, burnin, seed, hist.data(), am.data(),
-                     as.data(), nullptr, o ? o->stream : nullptr, &kms);
+                     as.data(), nullptr, o ? o->stream : nullptr, &kms, groups, ghist.data());
   if (st) return st;
   double ratios[kPtMaxRungs];
   const double est = pt_estimate_from_hist(variant, n, M, beta.data(), hist.data(), ratios);
   *out = est;
+  // relative standard error: spread of the group estimates, over their mean and sqrt(groups)
+  double rel_se = 0.0;
+  if (groups > 1) {
+    std::vector<double> eg(groups);
+    double mean = 0.0;
+    for (int g = 0; g < groups; ++g) {
+      eg[g] = pt_estimate_from_hist(variant, n, M, beta.data(), ghist.data() + (size_t)g * M * nb,
+                                    nullptr);
+      mean += eg[g] / groups;
+    }
+    double var = 0.0;
+    for (int g = 0; g < groups; ++g) var += (eg[g] - mean) * (eg[g] - mean) / (groups - 1);
+    rel_se = mean > 0.0 ? std::sqrt(var / groups) / mean : std::numeric_limits<double>::quiet_NaN();
+  }
   if (rep) {
     std::memset(rep, 0, sizeof(*rep));
     rep->rungs = M;
@@ -438,6 +472,7 @@ int pt_estimate_impl(int variant, int n, uint64_t budget, const sk_pt_opts* o, d
       rep->acc_swap[j] = j + 1 < M ? (double)as[j] / tries : 0.0;
     }
     rep->estimate = est;
+    rep->rel_stderr = rel_se;
     rep->kernel_ms = kms;
     rep->tune_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     rep->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

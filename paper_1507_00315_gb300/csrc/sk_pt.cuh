@@ -28,6 +28,7 @@ namespace sk {
 
 constexpr int kPtMaxRungs = 32;
 constexpr int kPtMaxN = 40;
+constexpr int kPtErrorGroups = 16;   // ladder groups behind pt_estimate's standard error
 
 struct PtParams {
   int n, delta, M, bins;          // bins = 2n
@@ -36,7 +37,13 @@ struct PtParams {
   unsigned iters, burnin;
   unsigned key0, key1;
   unsigned rk[20];                // Philox round keys: (key0 + r W0, key1 + r W1), r = 0..9
+  int groups;                     // energy histograms kept per group of ladders (>= 1)
 };
+
+// Ladder group of a ladder: `groups` equal runs of consecutive ladders.
+__host__ __device__ inline int pt_group(int ladder, int ladders, int groups) {
+  return (int)((long long)ladder * groups / ladders);
+}
 
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1) {
 #pragma unroll

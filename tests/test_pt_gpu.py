@@ -58,6 +58,22 @@ def test_pt_estimate_small_orders(skolem_table, langford_table):
         assert abs(est / table[n] - 1) < 0.01, (variant, n, est, rep["acc_swap"])
 
 
+def test_grouped_histograms_and_standard_error(skolem_table):
+    # pt_estimate keeps its histograms per group of ladders: pooled, they are
+    # the plain run's histogram (same ladder, seed and burn-in), and the
+    # spread of the group estimates gives the standard error
+    beta = sk.tune_ladder(0, 9, 16, 16.0, 0)
+    est, rep = sk.pt_estimate(0, 9, 20000, ladders=1024, seed=5, beta=beta)
+    res = sk.pt_run(0, 9, beta, 1024, 20000, 2000, 5)
+    want = oracle.pt_estimate_from_hist(res["hist"], beta, 0, 9)
+    assert abs(est / want - 1) < 1e-12
+    assert 0.0 < rep["rel_stderr"] < 0.01
+    # equilibrated at this order: the error is statistical
+    assert abs(est / skolem_table[9] - 1) < 5 * rep["rel_stderr"] + 2e-3, rep["rel_stderr"]
+    one = sk.pt_estimate(0, 9, 2000, ladders=1, seed=5, beta=beta)[1]
+    assert one["rel_stderr"] == 0.0                 # a single ladder: no groups
+
+
 def test_pt_estimate_n12_within_one_percent(skolem_table):
     # Algorithm 2 starts from random configurations; at n = 12 the low
     # temperatures need ~1e5 iterations to forget them (40k: -5 %, 160k:
