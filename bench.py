@@ -295,9 +295,10 @@ def run_extra(args, world, rank, local):
 # 32x32->64 products, counted as two operations each, two three-input xors
 # and two key additions: 80); the move (pair and slot by two multiply-highs,
 # the skip of the current slot, four occupancy updates with their empty-bin
-# tests, the energy change, the threshold test, the slot write or the undo:
-# 18); the histogram count (3); the exchange decision, made for half of the
-# rungs per iteration (energy difference, threshold test, label update: 2).
+# tests, the energy change, the threshold test, the slot write: 18); the
+# histogram count (3); the exchange decision, made for half of the rungs per
+# iteration (energy difference, threshold test, the swap: 2).  The count is a
+# property of the algorithm, not of the kernel's form.
 PT_OPS_PER_LANE_ITERATION = 80 + 18 + 3 + 2
 
 EXACT_S = {16: 700078384, 20: 5717789399488, 24: 102388058845620672,
