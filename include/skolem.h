@@ -268,6 +268,17 @@ int sk_pt_run(int variant, int n, int M, const double *beta, int L, uint64_t ite
               uint64_t burnin, uint64_t seed, uint64_t *hist, uint64_t *acc_move,
               uint64_t *acc_swap, uint8_t *final_slots);
 
+/* The estimator of pt_estimate on host histograms; host code only, no device
+ * needed.  hist: `groups` >= 1 histograms of M x (2n+1) energy counts (groups x
+ * M x (2n+1), host), e.g. sk_pt_run's over separate sets of ladders.  out:
+ * 1/2 Z(0) prod_j Ratio(j) of their sum (as pt_estimate); ratios (M, may be
+ * NULL): the Ratio(j) of the sum; rel_stderr (may be NULL): with groups >= 2
+ * the relative standard error of out from the spread of the group estimates
+ * (as sk_pt_report.rel_stderr), else 0.  Same variant / n / ladder checks as
+ * pt_estimate (SK_EINVAL). */
+int sk_pt_estimate_hist(int variant, int n, int M, const double *beta, int groups,
+                        const uint64_t *hist, double *out, double *ratios, double *rel_stderr);
+
 /* The pilot-tuned ladder pt_estimate uses when opts->beta is NULL. */
 int sk_pt_tune_ladder(int variant, int n, int rungs, double beta_max, uint64_t seed,
                       double *beta);

@@ -191,6 +191,9 @@ def lib():
                                         u64, u64, u64, vp, vp, vp, vp]
         L.sk_pt_tune_ladder.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                         u64, vp]
+        L.sk_pt_estimate_hist.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int,
+                                          vp, ctypes.POINTER(ctypes.c_double), vp,
+                                          ctypes.POINTER(ctypes.c_double)]
         L.sk_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, u64,
                                     ctypes.POINTER(ctypes.c_void_p)]
         L.sk_mlp_destroy.argtypes = [vp]
@@ -387,6 +390,27 @@ def pt_run(variant, n: int, beta, ladders: int, iters: int, burnin: int, seed: i
     if st != SK_OK:
         raise SkolemError(st, "sk_pt_run")
     return {"hist": hist, "acc_move": am, "acc_swap": asw, "final_slots": fin}
+
+
+def pt_estimate_hist(variant, n: int, beta, hist):
+    """sk_pt_estimate_hist: (estimate, ratios, rel_stderr) of energy histograms
+    shaped (M, 2n+1) or (groups, M, 2n+1); host code, no device."""
+    np = _np()
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    h = np.ascontiguousarray(hist, dtype=np.uint64)
+    M = b.shape[0]
+    if h.ndim == 2:
+        h = h[None]
+    if h.ndim != 3 or h.shape[1:] != (M, 2 * n + 1):
+        raise ValueError("hist must be (M, 2n+1) or (groups, M, 2n+1)")
+    out, se = ctypes.c_double(), ctypes.c_double()
+    ratios = np.zeros(M, dtype=np.float64)
+    st = lib().sk_pt_estimate_hist(_variant(variant), n, M, b.ctypes.data, h.shape[0],
+                                   h.ctypes.data, ctypes.byref(out), ratios.ctypes.data,
+                                   ctypes.byref(se))
+    if st != SK_OK:
+        raise SkolemError(st, "sk_pt_estimate_hist")
+    return out.value, ratios, se.value
 
 
 def tune_ladder(variant, n: int, rungs: int = 32, beta_max: float = 32.0, seed: int = 0):

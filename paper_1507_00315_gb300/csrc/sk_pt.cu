@@ -346,7 +346,50 @@ double pt_estimate_from_hist(int variant, int n, int M, const double* beta, cons
   return (double)std::exp(logs);
 }
 
+// Pooled estimate of `groups` histograms (groups x M x (2n+1)) and, with
+// groups >= 2, the relative standard error of it: the sample standard
+// deviation of the group estimates over their mean and sqrt(groups) (NaN
+// when the mean is 0).
+double pt_pooled_estimate(int variant, int n, int M, const double* beta, int groups,
+                          const uint64_t* ghist, double* ratios, double* rel_stderr) {
+  const size_t per = (size_t)M * (2 * n + 1);
+  std::vector<uint64_t> pooled(per, 0);
+  for (int g = 0; g < groups; ++g)
+    for (size_t i = 0; i < per; ++i) pooled[i] += ghist[(size_t)g * per + i];
+  const double est = pt_estimate_from_hist(variant, n, M, beta, pooled.data(), ratios);
+  if (rel_stderr) {
+    *rel_stderr = 0.0;
+    if (groups > 1) {
+      std::vector<double> eg(groups);
+      double mean = 0.0;
+      for (int g = 0; g < groups; ++g) {
+        eg[g] = pt_estimate_from_hist(variant, n, M, beta, ghist + (size_t)g * per, nullptr);
+        mean += eg[g] / groups;
+      }
+      double var = 0.0;
+      for (int g = 0; g < groups; ++g) var += (eg[g] - mean) * (eg[g] - mean) / (groups - 1);
+      *rel_stderr = mean > 0.0 ? std::sqrt(var / groups) / mean
+                               : std::numeric_limits<double>::quiet_NaN();
+    }
+  }
+  return est;
+}
+
 }  // namespace sk
+
+extern "C" int sk_pt_estimate_hist(int variant, int n, int M, const double* beta, int groups,
+                                   const uint64_t* hist, double* out, double* ratios,
+                                   double* rel_stderr) {
+  if (variant != SK_SKOLEM && variant != SK_LANGFORD) return SK_EINVAL;
+  if (n < 2 || n > sk::kPtMaxN || M < 1 || M > sk::kPtMaxRungs || groups < 1) return SK_EINVAL;
+  if (!beta || !hist || !out) return SK_EINVAL;
+  for (int j = 0; j < M; ++j) {
+    if (!(beta[j] >= 0.0) || !std::isfinite(beta[j])) return SK_EINVAL;
+    if (j && beta[j] < beta[j - 1]) return SK_EINVAL;
+  }
+  *out = sk::pt_pooled_estimate(variant, n, M, beta, groups, hist, ratios, rel_stderr);
+  return SK_OK;
+}
 
 extern "C" int sk_pt_run(int variant, int n, int M, const double* beta, int L, uint64_t iters,
                          uint64_t burnin, uint64_t seed, uint64_t* hist, uint64_t* acc_move,
@@ -442,22 +485,11 @@ int pt_estimate_impl(int variant, int n, uint64_t budget, const sk_pt_opts* o, d
                      as.data(), nullptr, o ? o->stream : nullptr, &kms, groups, ghist.data());
   if (st) return st;
   double ratios[kPtMaxRungs];
-  const double est = pt_estimate_from_hist(variant, n, M, beta.data(), hist.data(), ratios);
-  *out = est;
-  // relative standard error: spread of the group estimates, over their mean and sqrt(groups)
   double rel_se = 0.0;
-  if (groups > 1) {
-    std::vector<double> eg(groups);
-    double mean = 0.0;
-    for (int g = 0; g < groups; ++g) {
-      eg[g] = pt_estimate_from_hist(variant, n, M, beta.data(), ghist.data() + (size_t)g * M * nb,
-                                    nullptr);
-      mean += eg[g] / groups;
-    }
-    double var = 0.0;
-    for (int g = 0; g < groups; ++g) var += (eg[g] - mean) * (eg[g] - mean) / (groups - 1);
-    rel_se = mean > 0.0 ? std::sqrt(var / groups) / mean : std::numeric_limits<double>::quiet_NaN();
-  }
+  const double est = groups > 1
+      ? pt_pooled_estimate(variant, n, M, beta.data(), groups, ghist.data(), ratios, &rel_se)
+      : pt_estimate_from_hist(variant, n, M, beta.data(), hist.data(), ratios);
+  *out = est;
   if (rep) {
     std::memset(rep, 0, sizeof(*rep));
     rep->rungs = M;
