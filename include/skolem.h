@@ -340,6 +340,23 @@ int sk_pt_run_learned(int variant, int n, int M, const double *beta, int L, uint
 int skolem_item_residues(int variant, int n, int m, uint64_t q_lo, uint64_t count,
                          int nprimes, const uint64_t *primes, uint64_t *out);
 
+/* The host step after the sum, for a sum computed in parts -- disjoint
+ * ranges of work items on different GPUs, each part's item residues added
+ * modulo each prime -- with no device: residues (host, parts x nprimes,
+ * row-major, each in [0, p_i)) are added modulo each prime into the residues
+ * of the whole sum over the 2^{2n-1} assignments of Lemma 2.2 (the parts must
+ * cover every work item once), then rebuilt by the CRT with skolem_count_ex's
+ * checks (lower half of the CRT range, divisibility by 2^{2n-1}, agreement
+ * with a fourth prime) and put in `convention` (SK_COUNT_*).  primes: NULL
+ * for the defaults, else nprimes moduli as in sk_count_opts.  SK_EMISMATCH
+ * when a check fails, e.g. a residue that is wrong modulo one prime but not
+ * the others; a part left out or added twice is in general NOT caught (work
+ * item sums are themselves multiples of 2^{2n-1}), so covering every item
+ * exactly once is the caller's part.  SK_EINVAL for bad arguments. */
+int sk_count_from_residues(int variant, int n, int convention, int nprimes,
+                           const uint64_t *primes, uint64_t parts, const uint64_t *residues,
+                           sk_u128 *out);
+
 /* skolem_item_residues with a choice of arithmetic form (SK_ARITH_*). */
 int skolem_item_residues_ex(int variant, int n, int m, uint64_t q_lo, uint64_t count,
                             int nprimes, const uint64_t *primes, int arith, uint64_t *out);

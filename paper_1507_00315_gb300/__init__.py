@@ -169,6 +169,9 @@ def lib():
                                            ctypes.c_uint64, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_uint64),
                                            ctypes.POINTER(ctypes.c_uint64)]
+        L.sk_count_from_residues.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint64,
+                                             ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(U128)]
         L.skolem_item_residues_ex.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                               ctypes.POINTER(ctypes.c_uint64), ctypes.c_int,
@@ -300,6 +303,28 @@ def item_residues(variant, n: int, m: int, q_lo: int, count_: int, primes, arith
     if st != SK_OK:
         raise SkolemError(st, "skolem_item_residues")
     return [list(out[i * k:(i + 1) * k]) for i in range(count_)]
+
+
+def count_from_residues(variant, n: int, residues, primes=None,
+                        convention=REFLECTIONS_IDENTIFIED) -> int:
+    """sk_count_from_residues: the exact count from the residues of a sum
+    computed in parts (rows: parts, columns: one residue per prime, e.g. the
+    item residues of each GPU's item range added modulo each prime); host
+    code, no device."""
+    rows = [list(r) for r in residues]
+    if not rows:
+        raise ValueError("no residues")
+    k = len(primes) if primes is not None else len(rows[0])
+    if any(len(r) != k for r in rows):
+        raise ValueError("residues must be rows of one residue per prime")
+    flat = (ctypes.c_uint64 * (len(rows) * k))(*[int(v) for r in rows for v in r])
+    P = (ctypes.c_uint64 * k)(*primes) if primes is not None else None
+    out = U128()
+    st = lib().sk_count_from_residues(_variant(variant), n, convention, k, P, len(rows), flat,
+                                      ctypes.byref(out))
+    if st != SK_OK:
+        raise SkolemError(st, "sk_count_from_residues")
+    return out.value()
 
 
 def item_residues_noalloc(variant, n: int, m: int, q_lo: int, count_: int, primes, stream=None):

@@ -551,6 +551,36 @@ extern "C" int skolem_count_ex(int variant, int n, const sk_count_opts* opts, sk
   return sk::count_impl(variant, n, opts, out, rep);
 }
 
+// The host step after the sums, for sums computed in parts (work-item ranges
+// on different GPUs): the parts' residues added modulo each prime, then the
+// CRT, checks and output convention of skolem_count_ex.  Host code only.
+extern "C" int sk_count_from_residues(int variant, int n, int convention, int nprimes,
+                                      const uint64_t* primes, uint64_t parts,
+                                      const uint64_t* residues, sk_u128* out) {
+  if (variant < SK_SKOLEM || variant > SK_HOOKED || n < 1 || n > sk::kMaxN) return SK_EINVAL;
+  if (convention != SK_COUNT_REFLECTIONS_IDENTIFIED && convention != SK_COUNT_ALL)
+    return SK_EINVAL;
+  if (!residues || !out || parts == 0) return SK_EINVAL;
+  sk_count_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.nprimes = nprimes;
+  if (primes)
+    for (int i = 0; i < nprimes && i < SK_MAX_PRIMES; ++i) o.primes[i] = primes[i];
+  int k = 0;
+  uint64_t pv[SK_MAX_PRIMES] = {};
+  sk::Primes P;
+  int st = sk::prepare_primes(&o, &k, pv, &P);
+  if (st) return st;
+  uint64_t H[SK_MAX_PRIMES] = {};
+  for (uint64_t q = 0; q < parts; ++q)
+    for (int i = 0; i < k; ++i) {
+      const uint64_t r = residues[q * (uint64_t)k + i];
+      if (r >= pv[i]) return SK_EINVAL;
+      H[i] = (uint64_t)(((unsigned __int128)H[i] + r) % pv[i]);
+    }
+  return sk::finalize_count(variant, n, convention, k, pv, H, out);
+}
+
 extern "C" int skolem_item_residues(int variant, int n, int m, uint64_t q_lo, uint64_t count,
                                     int nprimes, const uint64_t* primes, uint64_t* out) {
   return sk::item_residues_impl(variant, n, m, q_lo, count, nprimes, primes, SK_ARITH_LIMBS, out);
