@@ -37,6 +37,19 @@ def test_trajectory_equals_oracle(variant, n, M, L, iters, burnin, seed):
     assert np.array_equal(got["final_slots"], want["final_slots"])
 
 
+@pytest.mark.parametrize("variant,n,iters", [(0, 16, 200), (1, 24, 150)])
+def test_trajectory_equals_oracle_at_full_size(variant, n, iters):
+    # the tempering workload's launch: 32 rungs x 4096 ladders, every ladder
+    # resident at once; a short run so the oracle finishes in seconds
+    beta = list(np.linspace(0.0, 32.0, 32))
+    got = sk.pt_run(variant, n, beta, 4096, iters, iters // 10, 99, want_final=True)
+    want = oracle.pt_run(variant, n, beta, 4096, iters, iters // 10, 99, want_final=True)
+    assert np.array_equal(got["hist"], want["hist"])
+    assert np.array_equal(got["acc_move"], want["acc_move"])
+    assert np.array_equal(got["acc_swap"], want["acc_swap"])
+    assert np.array_equal(got["final_slots"], want["final_slots"])
+
+
 @pytest.mark.parametrize("variant,n", [(0, 4), (0, 5), (1, 4)])
 def test_ratios_against_exact_partition_function(variant, n):
     beta = np.array([0.0, 0.5, 1.0, 1.6, 2.4, 3.5, 5.0, 8.0])
