@@ -131,6 +131,15 @@ typedef struct sk_count_report {
   int symmetry;                /* SK_SYMMETRY_* actually used */
 } sk_count_report;
 
+/* The plan skolem_count_ex would run for these options, without running it
+ * (host code only, no device): rep receives the moduli, walk and inner bits,
+ * arithmetic form, block size and grid (0: one wave), symmetry used, work
+ * items, terms and chunks_total (the launches of a checkpointed run); the
+ * fields that depend on the sums stay 0.  A zero class of Lemma 2.4 reports 0
+ * items and terms and complete = 1.  Same argument checks as
+ * skolem_count_ex. */
+int sk_count_plan(int variant, int n, const sk_count_opts *opts, sk_count_report *rep);
+
 /* Exact count of `variant` of order n (Lemma 2.1 with Lemma 2.2, evaluated in
  * Gray-code order, Sec. 2.1; residues modulo co-primes and the Chinese
  * remainder theorem, Sec. 2.2).  out (host): the count in the default

@@ -165,6 +165,8 @@ def lib():
         L.skolem_count.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(U128)]
         L.skolem_count_ex.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(CountOpts),
                                       ctypes.POINTER(U128), ctypes.POINTER(CountReport)]
+        L.sk_count_plan.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(CountOpts),
+                                    ctypes.POINTER(CountReport)]
         L.skolem_item_residues.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                            ctypes.c_uint64, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_uint64),
@@ -283,6 +285,18 @@ def count_ex(variant, n: int, **kw):
         raise SkolemError(st, f"skolem_count_ex({variant}, {n})")
     r = rep.as_dict()
     return (out.value() if r["complete"] else None), r
+
+
+def count_plan(variant, n: int, **kw):
+    """sk_count_plan: the report fields of the plan count_ex would run with
+    these keywords (walk and inner bits, items, terms, chunks_total, ...),
+    without running it; host code, no device."""
+    o = _opts(**kw)
+    rep = CountReport()
+    st = lib().sk_count_plan(_variant(variant), n, ctypes.byref(o), ctypes.byref(rep))
+    if st != SK_OK:
+        raise SkolemError(st, f"sk_count_plan({variant}, {n})")
+    return rep.as_dict()
 
 
 def int32_peak(mode: int = 0):

@@ -319,6 +319,55 @@ int limb_max_m(int delta, int n) {
   return kLimbMaxM[n][delta];
 }
 
+// Work items per launch: all of them without a checkpoint; with one, about
+// 2^37 terms per launch but at least 2^22 items, so that each of the ~80k
+// resident threads gets dozens of items and the last wave of a launch stays
+// short; opts->chunk_items overrides.  At most the job's items.
+static unsigned long long plan_chunk_items(const Plan& pl, const sk_count_opts* o, bool ckpt_on) {
+  unsigned long long chunk = (o && o->chunk_items) ? o->chunk_items : 0;
+  if (!chunk) {
+    if (ckpt_on) {
+      int lg = 37 - pl.m;
+      if (lg < 22) lg = 22;
+      chunk = lg >= 40 ? pl.items : (1ULL << lg);
+    } else {
+      chunk = pl.items;
+    }
+  }
+  if (chunk > pl.items) chunk = pl.items;
+  return chunk;
+}
+
+// The plan of skolem_count_ex without running it (host only): the fields of
+// the report that do not depend on the sums.
+static int plan_report(int variant, int n, const sk_count_opts* o, sk_count_report* rep) {
+  if (!rep) return SK_EINVAL;
+  Plan pl;
+  int st = make_plan(variant, n, o, &pl);
+  if (st) return st;
+  if (o && o->convention != SK_COUNT_REFLECTIONS_IDENTIFIED && o->convention != SK_COUNT_ALL)
+    return SK_EINVAL;
+  std::memset(rep, 0, sizeof(*rep));
+  rep->nprimes = pl.nprimes;
+  for (int i = 0; i < pl.nprimes; ++i) rep->primes[i] = pl.primes[i];
+  rep->walk_bits = pl.m;
+  rep->inner_bits = pl.U;
+  rep->arith = pl.arith;
+  rep->block_threads = pl.block_threads;
+  rep->grid = pl.grid;
+  rep->symmetry = pl.symmetry;
+  if (pl.sign < 0) {                      // a zero class of Lemma 2.4: nothing to evaluate
+    rep->complete = 1;
+    return SK_OK;
+  }
+  const bool ckpt_on = o && o->checkpoint_path && o->checkpoint_path[0];
+  const unsigned long long chunk = plan_chunk_items(pl, o, ckpt_on);
+  rep->items = pl.items;
+  rep->terms = pl.items << pl.m;
+  rep->chunks_total = (pl.items + chunk - 1) / chunk;
+  return SK_OK;
+}
+
 // Output convention of a coefficient C (pairings, reflections distinct).
 // Sec. 1.3: no sequence of order n > 1 is its own reflection; the single
 // Skolem sequence of order 1 (1,1) is.
@@ -380,20 +429,7 @@ int count_impl(int variant, int n, const sk_count_opts* o, sk_u128* out, sk_coun
     own_stream = true;
   }
   const bool ckpt_on = o && o->checkpoint_path && o->checkpoint_path[0];
-  unsigned long long chunk = (o && o->chunk_items) ? o->chunk_items : 0;
-  if (!chunk) {
-    if (ckpt_on) {
-      // about 2^37 terms per launch, but at least 2^22 items so that each of
-      // the ~80k resident threads gets dozens of items and the last wave of a
-      // launch stays short
-      int lg = 37 - pl.m;
-      if (lg < 22) lg = 22;
-      chunk = lg >= 40 ? pl.items : (1ULL << lg);
-    } else {
-      chunk = pl.items;
-    }
-  }
-  if (chunk > pl.items) chunk = pl.items;
+  const unsigned long long chunk = plan_chunk_items(pl, o, ckpt_on);
   const unsigned long long nchunks = (pl.items + chunk - 1) / chunk;
   Ckpt ck;
   ck.have.assign(ckpt_on ? nchunks : 0, 0);
@@ -549,6 +585,10 @@ extern "C" int skolem_count(int variant, int n, sk_u128* out) {
 extern "C" int skolem_count_ex(int variant, int n, const sk_count_opts* opts, sk_u128* out,
                                sk_count_report* rep) {
   return sk::count_impl(variant, n, opts, out, rep);
+}
+
+extern "C" int sk_count_plan(int variant, int n, const sk_count_opts* opts, sk_count_report* rep) {
+  return sk::plan_report(variant, n, opts, rep);
 }
 
 // The host step after the sums, for sums computed in parts (work-item ranges
