@@ -27,3 +27,9 @@ def test_operations_per_term():
 def test_tempering_operations():
     # Philox-4x32-10 (80) + move (18) + histogram (3) + half an exchange (2)
     assert bench.PT_OPS_PER_LANE_ITERATION == 103
+
+
+def test_oracle_sample_shape():
+    # the CPU baseline: (terms/s, cores, description, measured seconds)
+    v, cores, sample, dt = bench.oracle_sample(seconds_target=0.3)
+    assert v > 0 and cores >= 1 and dt > 0 and "work items of S(20)/L(20)" in sample
