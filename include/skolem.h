@@ -320,12 +320,25 @@ int sk_mlp_forward(void *model, const uint8_t *slots, int B, float *logits);
  * n_params, same layout as the parameters); the model is not updated. */
 int sk_mlp_loss_grad(void *model, const uint8_t *slots, int B, float beta_star, float *loss,
                      float *grads);
-/* Adam training (lr, betas 0.9 / 0.999) on `count` states (host, count x n),
- * `epochs` passes in minibatches of `batch` (multiple of 128) in an order
- * shuffled by `seed`.  final_loss: mean loss of the last epoch; ms: device
- * time (both may be NULL). */
+/* Adam (Kingma & Ba 2015: lr, betas 0.9 / 0.999, eps 1e-8, bias-corrected
+ * moments) on `count` states (host, count x n), `epochs` passes in
+ * minibatches of `batch` (multiple of 128) in an order shuffled by `seed`,
+ * or in the given order when seed == SK_MLP_KEEP_ORDER.  Each minibatch is
+ * one step: forward, loss and gradients (as sk_mlp_loss_grad), the update of
+ * the FP32 masters and moments, and the refresh of the BF16 weight copies.
+ * final_loss: mean loss of the last epoch; ms: device time (both may be
+ * NULL). */
+#define SK_MLP_KEEP_ORDER UINT64_MAX
 int sk_mlp_train(void *model, const uint8_t *states, uint64_t count, int epochs, int batch,
                  float lr, float beta_star, uint64_t seed, float *final_loss, double *ms);
+/* Training state of a model, each array (host, n_params floats, the
+ * parameter layout; any may be NULL): Adam's first and second moments, and
+ * the parameters the forward pass uses -- the BF16 copies of W1, W2, W3
+ * widened to float, and the FP32 biases.  *t (may be NULL): Adam steps taken
+ * since sk_mlp_create or the last sk_mlp_set_params (which zeroes the
+ * moments). */
+int sk_mlp_get_train_state(const void *model, float *adam_m, float *adam_v, float *used,
+                           int64_t *t);
 /* Selects the forward GEMM path of a model: 1 (default) the 5th-generation
  * tensor cores (tcgen05, accumulators in tensor memory), 0 warp-level
  * mma.sync.  sk_mlp_check returns SK_ETIMEOUT if a tensor-core wait of the

@@ -124,6 +124,7 @@ class TuneResult(ctypes.Structure):
 
 BATCH_PERSISTENT, BATCH_PER_JOB = 0, 1
 PT_PLAIN, PT_LEARNED = 0, 1
+MLP_KEEP_ORDER = (1 << 64) - 1      # sk_mlp_train seed: minibatches in the given order
 PT_MAX_RUNGS = 32
 
 
@@ -208,6 +209,7 @@ def lib():
         L.sk_mlp_get_params.argtypes = [vp, vp]
         L.sk_mlp_forward.argtypes = [vp, vp, ctypes.c_int, vp]
         L.sk_mlp_loss_grad.argtypes = [vp, vp, ctypes.c_int, ctypes.c_float, vp, vp]
+        L.sk_mlp_get_train_state.argtypes = [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
         L.sk_mlp_set_gemm.argtypes = [vp, ctypes.c_int]
         L.sk_mlp_check.argtypes = [vp]
         L.sk_mlp_train.argtypes = [vp, vp, u64, ctypes.c_int, ctypes.c_int, ctypes.c_float,
@@ -555,6 +557,21 @@ class Mlp:
         if st != SK_OK:
             raise SkolemError(st, "sk_mlp_loss_grad")
         return float(loss[0]), g
+
+    def train_state(self):
+        """sk_mlp_get_train_state: dict(m, v, used, t) -- Adam's moments, the
+        parameters the forward uses (BF16 weight copies widened, FP32 biases),
+        and the step count; host parameter layout."""
+        np = _np()
+        m = np.zeros(self.n_params, dtype=np.float32)
+        v = np.zeros(self.n_params, dtype=np.float32)
+        u = np.zeros(self.n_params, dtype=np.float32)
+        t = ctypes.c_int64()
+        st = lib().sk_mlp_get_train_state(self.handle, m.ctypes.data, v.ctypes.data, u.ctypes.data,
+                                          ctypes.byref(t))
+        if st != SK_OK:
+            raise SkolemError(st, "sk_mlp_get_train_state")
+        return {"m": m, "v": v, "used": u, "t": t.value}
 
     def train(self, states, epochs: int = 1, batch: int = 4096, lr: float = 1e-3,
               beta_star: float = 2.0, seed: int = 0):

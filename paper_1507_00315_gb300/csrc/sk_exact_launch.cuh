@@ -16,9 +16,36 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "sk_exact.cuh"
 
 namespace sk {
+
+// Host-side caches of launch shapes are kept per device (a process may drive
+// several GPUs, each current in its own host threads) and read and written
+// atomically; concurrent first calls compute and store the same value.
+constexpr int kMaxDevices = 64;
+
+// Resident CTAs per SM of one kernel, per device and block size (multiples of
+// 32 up to 256).
+struct OccupancyCache {
+  std::atomic<int> per_sm[kMaxDevices][9];
+};
+
+// SM count of device `dev` (looked up once per device).
+inline int device_sm_count(int dev) {
+  static std::atomic<int> cache[kMaxDevices];
+  const bool keyed = dev >= 0 && dev < kMaxDevices;
+  int v = keyed ? cache[dev].load(std::memory_order_relaxed) : 0;
+  if (v <= 0) {
+    v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (v <= 0) return 1;
+    if (keyed) cache[dev].store(v, std::memory_order_relaxed);
+  }
+  return v;
+}
 
 // Scratch words of one launch (device memory, zeroed before the launch).
 struct ExactScratch {
@@ -159,27 +186,27 @@ __global__ void __launch_bounds__(256, SK_EXACT_MIN_BLOCKS)
   work_loop<MontItem<DELTA, N, NPR>>(job, P, NPR, item_lo, item_hi, scr, item_res);
 }
 
-// Grid: SMs x resident CTAs per SM, never more warps than 32-item chunks.
+// Grid: SMs x resident CTAs per SM of the current device, never more warps
+// than 32-item chunks.
 template <class K>
-cudaError_t exact_grid(K kernel, const ExactLaunch& L, size_t smem, int* blocks_per_sm_cache,
+cudaError_t exact_grid(K kernel, const ExactLaunch& L, size_t smem, OccupancyCache& occ,
                        int* grid_out) {
-  static int sms = 0;
   const int bt = L.block_threads;
   if (bt < 32 || bt > 256 || (bt & 31)) return cudaErrorInvalidValue;
   int grid = L.grid;
   if (grid <= 0) {
-    if (!sms) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
-    if (!blocks_per_sm_cache[bt]) {
-      int nb = 0;
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, bt, smem);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const bool keyed = dev >= 0 && dev < kMaxDevices;
+    int nb = keyed ? occ.per_sm[dev][bt / 32].load(std::memory_order_relaxed) : 0;
+    if (nb <= 0) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, bt, smem);
       if (e != cudaSuccess) return e;
-      blocks_per_sm_cache[bt] = nb > 0 ? nb : 1;
+      if (nb <= 0) nb = 1;
+      if (keyed) occ.per_sm[dev][bt / 32].store(nb, std::memory_order_relaxed);
     }
-    grid = sms * blocks_per_sm_cache[bt];
+    grid = device_sm_count(dev) * nb;
     unsigned long long chunks = (L.item_hi - L.item_lo + 31) / 32;
     unsigned long long warps_per_block = (unsigned long long)bt / 32;
     unsigned long long need = (chunks + warps_per_block - 1) / warps_per_block;
@@ -191,7 +218,7 @@ cudaError_t exact_grid(K kernel, const ExactLaunch& L, size_t smem, int* blocks_
 
 template <int DELTA, int N, int NPR>
 cudaError_t launch_exact(const ExactLaunch& L) {
-  static int bps[257] = {0};
+  static OccupancyCache bps;
   if (L.nprimes != NPR) return cudaErrorInvalidValue;
   const size_t smem = (size_t)ws_len(DELTA, N) * kWsStride;
   int grid = 0;
@@ -204,7 +231,7 @@ cudaError_t launch_exact(const ExactLaunch& L) {
 
 template <int DELTA, int N>
 cudaError_t launch_limb(const ExactLaunch& L) {
-  static int bps[257] = {0};
+  static OccupancyCache bps;
   if (L.nprimes < 1 || L.nprimes > kMaxPrimes) return cudaErrorInvalidValue;
   const size_t smem = (size_t)ws_len(DELTA, N) * kWsStride;
   int grid = 0;

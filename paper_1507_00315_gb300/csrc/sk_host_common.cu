@@ -106,17 +106,22 @@ int crt_coefficient(int n, int nprimes, const uint64_t* p, const uint64_t* H, sk
 
 // ---------------------------------------------------------------- CRC-32
 
-uint32_t crc32(const void* data, size_t len) {
-  static uint32_t table[256];
-  static bool init = false;
-  if (!init) {
+namespace {
+struct Crc32Table {
+  uint32_t t[256];
+  Crc32Table() {
     for (uint32_t i = 0; i < 256; ++i) {
       uint32_t c = i;
       for (int k = 0; k < 8; ++k) c = (c & 1) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
-      table[i] = c;
+      t[i] = c;
     }
-    init = true;
   }
+};
+}  // namespace
+
+uint32_t crc32(const void* data, size_t len) {
+  static const Crc32Table tab;          // built once, thread-safe (function-local static)
+  const uint32_t* table = tab.t;
   const unsigned char* b = (const unsigned char*)data;
   uint32_t c = 0xFFFFFFFFu;
   for (size_t i = 0; i < len; ++i) c = table[(c ^ b[i]) & 0xFF] ^ (c >> 8);

@@ -11,9 +11,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <random>
 #include <vector>
 
+#include "sk_exact_launch.cuh"
 #include "sk_gemm.cuh"
 #include "sk_gemm_tc.cuh"
 #include "sk_host_common.h"
@@ -247,20 +249,24 @@ cudaError_t gemm_tc(const TcGemmArgs& g, const CUtensorMap& amap, const CUtensor
                     const CUtensorMap& cmap, int bf16, cudaStream_t s) {
   if (g.M % kTcBM || g.N % kTcBN || g.K % kTcBK || g.K > kTcMaxK || g.M <= 0)
     return cudaErrorInvalidValue;
-  static bool attr = false;
-  static int sms = 0;
-  if (!attr) {
+  // the shared-memory opt-in is a per-device function attribute: set it once
+  // per device, with that device current
+  int dev = 0;
+  cudaError_t e0 = cudaGetDevice(&dev);
+  if (e0 != cudaSuccess) return e0;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  static std::once_flag once[kMaxDevices];
+  static cudaError_t attr_err[kMaxDevices];
+  std::call_once(once[dev], [dev]() {
     cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<1>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(gemm_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                kTcSmem);
-    if (e != cudaSuccess) return e;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    attr = true;
-  }
+    attr_err[dev] = e;
+  });
+  if (attr_err[dev] != cudaSuccess) return attr_err[dev];
+  const int sms = device_sm_count(dev);
   // one CTA per SM, a whole number of CTAs per 256-wide column tile
   const int NT = g.N / kTcBN, MT = g.M / kTcBM;
   int per = sms / NT;
@@ -574,6 +580,41 @@ extern "C" int sk_mlp_get_params(const void* model, float* params) {
   return SK_OK;
 }
 
+extern "C" int sk_mlp_get_train_state(const void* model, float* adam_m, float* adam_v,
+                                      float* used, int64_t* t) {
+  const Mlp* m = (const Mlp*)model;
+  if (!m) return SK_EINVAL;
+  std::vector<float> d(m->nparams);
+  cudaError_t e = cudaSuccess;
+  if (adam_m) {
+    e = cudaMemcpy(d.data(), m->am, m->nparams * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return sk::cuda_status(e);
+    sk::pack_host(*m, d.data(), adam_m);
+  }
+  if (adam_v) {
+    e = cudaMemcpy(d.data(), m->av, m->nparams * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return sk::cuda_status(e);
+    sk::pack_host(*m, d.data(), adam_v);
+  }
+  if (used) {
+    // the biases enter the forward as FP32 masters, the weight matrices as
+    // their BF16 copies (widened exactly: a bf16 is the top half of a float)
+    e = cudaMemcpy(d.data(), m->mW1, m->nparams * 4, cudaMemcpyDeviceToHost);
+    const size_t nwb = (size_t)m->K1 * sk::kHidden + (size_t)sk::kHidden * sk::kHidden +
+                       (size_t)sk::kHidden * m->NMp;
+    std::vector<uint16_t> wb(nwb);
+    if (e == cudaSuccess) e = cudaMemcpy(wb.data(), m->W1, nwb * 2, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return sk::cuda_status(e);
+    for (size_t i = 0; i < nwb; ++i) {
+      const uint32_t u = (uint32_t)wb[i] << 16;
+      std::memcpy(&d[i], &u, 4);
+    }
+    sk::pack_host(*m, d.data(), used);
+  }
+  if (t) *t = m->adam_t;
+  return SK_OK;
+}
+
 extern "C" int sk_mlp_forward(void* model, const uint8_t* slots, int B, float* logits) {
   Mlp* m = (Mlp*)model;
   if (!m || !slots || !logits || B < 1 || B > m->max_batch) return SK_EINVAL;
@@ -637,7 +678,7 @@ int mlp_train_impl(Mlp& m, const uint8_t* states, uint64_t count, int epochs, in
   if (e == cudaSuccess) e = cudaEventRecord(e0, s);
   double last = 0.0;
   for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
-    std::shuffle(perm.begin(), perm.end(), rng);
+    if (seed != SK_MLP_KEEP_ORDER) std::shuffle(perm.begin(), perm.end(), rng);
     e = cudaMemcpyAsync(didx, perm.data(), count * sizeof(unsigned), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // perm is reused next epoch
     for (uint64_t st = 0; st < steps && e == cudaSuccess; ++st) {

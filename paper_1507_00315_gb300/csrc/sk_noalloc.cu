@@ -43,7 +43,6 @@ static_assert(sizeof(ExactScratch) <= kHeaderWords * 8, "launch record must fit 
 
 static __device__ __align__(256) unsigned long long sk_noalloc_scratch[kNoAllocWords];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 unsigned long long* g_scratch_ptr[kMaxDevices] = {nullptr};
 

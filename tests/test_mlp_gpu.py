@@ -118,3 +118,68 @@ def test_tensor_memory_and_mma_sync_paths_agree(variant, n, batch):
     model.set_gemm(False)
     b = model.forward(slots)
     assert np.abs(a - b).max() <= 1e-2 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("variant,n", [(0, 8), (1, 12)])
+def test_training_steps_match_adam_in_fp64(variant, n):
+    # Two sk_mlp_train steps on one fixed minibatch of 256 states (given
+    # order, so each step sees exactly the batch sk_mlp_loss_grad sees; at 256
+    # rows the backward has no split-K and one column-sum block, so the GPU's
+    # gradient is the same bits in both calls).  After each step the FP32
+    # masters and both moments must equal mlp_ref.adam_step applied in FP64
+    # to the pre-step state and that gradient, and the BF16 weight copies the
+    # forward uses must be the masters rounded to nearest-even bf16 exactly.
+    # The gradient itself is checked against the FP64 backward
+    # (mlp_ref.loss_and_grads) at the bf16 tolerance of
+    # test_gradients_match_fp64.
+    d = si.differences(variant, n)
+    _, nslot = mlp_ref.move_table(n, d)
+    nm = int(nslot.sum())
+    B, lr, beta_star = 256, 1e-3, 2.0
+    model = sk.Mlp(variant, n, B, seed=2)
+    params = [si.bf16_round(p) for p in si.mlp_params(17, 2 * n, 256, nm)]
+    model.set_params(_flat(params))
+    slots = si.random_slots(19, B, n, d)
+    x = mlp_ref.occupancy(slots, n, d)
+    mask = mlp_ref.valid_mask(slots, n, d)
+    target = mlp_ref.target_distribution(slots, n, d, beta_star)
+    names = ["W1", "b1", "W2", "b2", "W3", "b3"]
+    st0 = model.train_state()
+    assert st0["t"] == 0 and not st0["m"].any() and not st0["v"].any()
+    w = model.get_params().astype(np.float64)
+    m = np.zeros_like(w)
+    v = np.zeros_like(w)
+    for t in (1, 2):
+        _, g = model.loss_grad(slots, beta_star)
+        _, gr = mlp_ref.loss_and_grads(x, *_unflat(w, n, nm), mask, target)
+        for name, a in zip(names, _unflat(g, n, nm)):
+            rel = np.linalg.norm(a - gr[name]) / max(np.linalg.norm(gr[name]), 1e-12)
+            assert rel < 3e-2, (t, name, rel)
+        model.train(slots, epochs=1, batch=B, lr=lr, beta_star=beta_star, seed=sk.MLP_KEEP_ORDER)
+        # the kernel's betas are the float32 values of 0.9 and 0.999
+        # (0.999f is 1.3e-5 away from 0.999 in relative terms); the reference
+        # takes the same two numbers
+        w_ref, m_ref, v_ref = mlp_ref.adam_step(w, g.astype(np.float64), m, v, t, lr,
+                                                b1=float(np.float32(0.9)),
+                                                b2=float(np.float32(0.999)))
+        w_gpu = model.get_params().astype(np.float64)
+        st = model.train_state()
+        assert st["t"] == t
+        # FP32 arithmetic of one update: a few ulp of each moment (m can
+        # cancel at t = 2, so its tolerance is scaled by the largest |m|).
+        # The step lr * mhat / (sqrt(vhat) + eps) is at most lr here (by
+        # Cauchy-Schwarz over the two gradients), and the host's fp32 bias
+        # correction 1 - beta2^t is off by up to 2^-24 / (1 - beta2^t) =
+        # 1.5e-5 relative at t = 2, 7.5e-6 of the step after the square root.
+        assert np.allclose(st["m"], m_ref, rtol=1e-5, atol=1e-6 * np.abs(m_ref).max()), t
+        assert np.allclose(st["v"], v_ref, rtol=1e-5, atol=1e-30), t
+        err = np.abs(w_gpu - w_ref)
+        tol = 2e-5 * lr + 2.0 ** -22 * np.abs(w_ref)
+        assert (err <= tol).all(), (t, float(err.max()), int((err > tol).sum()))
+        assert np.abs(w_gpu - w).max() > 0.5 * lr           # the step moved the weights
+        used = _unflat(st["used"], n, nm)
+        masters = _unflat(w_gpu, n, nm)
+        for i, name in enumerate(names):
+            want = si.bf16_round(masters[i]) if name.startswith("W") else masters[i]
+            assert np.array_equal(used[i], want), (t, name)
+        w, m, v = w_gpu, st["m"].astype(np.float64), st["v"].astype(np.float64)

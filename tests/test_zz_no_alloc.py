@@ -10,6 +10,7 @@ import ctypes
 
 import pytest
 
+import oracle
 import paper_1507_00315_gb300 as sk
 
 pytestmark = pytest.mark.gpu
@@ -34,6 +35,12 @@ def test_noalloc_matches_allocating_entry_point_twice(variant, n, m, q_lo, count
         st, got = _noalloc(variant, n, m, q_lo, count, primes)
         assert st == sk.SK_OK
         assert got == want
+    # and, independently of the allocating path, the CPU oracle's block sums
+    # (Lemma 2.1's summand over each item) for the first, last and some
+    # inner items
+    for i in sorted({0, 1, count // 3, count // 2, count - 2, count - 1}):
+        for j, p in enumerate(primes):
+            assert got[i][j] == oracle.partial_sum_mod(variant, n, m, q_lo + i, p), (i, p)
 
 
 def test_noalloc_different_calls_in_a_row():
