@@ -56,6 +56,9 @@ def _load():
             lib.orc_summand.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, u64p]
             lib.orc_partial_sum_mod.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_uint64, ctypes.c_uint64, u64p]
+            lib.orc_ie_count.argtypes = [ctypes.c_int, ctypes.c_int, u64p]
+            lib.orc_ie_partial_sum_mod.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_uint64, ctypes.c_uint64, u64p]
             lib.orc_philox4x32_10.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             lib.orc_pt_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                        ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
@@ -142,6 +145,25 @@ def partial_sum_mod(variant: int, n: int, m: int, q: int, p: int) -> int:
     lib = _load()
     out = ctypes.c_uint64()
     _check(lib.orc_partial_sum_mod(variant, n, m, q, p, ctypes.byref(out)), "partial_sum_mod")
+    return out.value
+
+
+def ie_count(variant: int, n: int) -> int:
+    """Inclusion-exclusion count (Sec. 2, third approach): the number of
+    sequences with reflections distinct, from the alternating sum over the
+    sets of avoided positions."""
+    lib = _load()
+    out = (ctypes.c_uint64 * 2)()
+    _check(lib.orc_ie_count(variant, n, out), "ie_count")
+    return out[0] | (out[1] << 64)
+
+
+def ie_partial_sum_mod(variant: int, n: int, m: int, q: int, p: int) -> int:
+    """The inclusion-exclusion sum over one block of sets (the low m of the
+    2n position variables run, the rest fixed by q), modulo p."""
+    lib = _load()
+    out = ctypes.c_uint64()
+    _check(lib.orc_ie_partial_sum_mod(variant, n, m, q, p, ctypes.byref(out)), "ie_partial_sum_mod")
     return out.value
 
 

@@ -23,6 +23,13 @@
  *                            (the low m free variables run, the rest fixed),
  *                            reduced modulo a given prime (Sec. 2.2: residues
  *                            modulo co-primes).
+ *   orc_ie_count          -- the inclusion-exclusion count (Sec. 2, the
+ *                            third approach, after Larsen): over every set S
+ *                            of avoided positions, (-1)^{|S|} times the
+ *                            number of pairings of the universe (overlaps
+ *                            allowed) that avoid S.
+ *   orc_ie_partial_sum_mod -- the same sum over one block of sets, reduced
+ *                            modulo a given prime.
  *   orc_philox4x32_10     -- the Philox-4x32-10 counter-based generator of
  *                            Salmon, Moraes, Dror, Shaw (SC'11), written from
  *                            its published definition.
@@ -282,6 +289,92 @@ int orc_partial_sum_mod(int variant, int n, int m, uint64_t q, uint64_t p, uint6
         }
         if (sign < 0) prod = prod ? p - prod : 0;
         acc = (acc + prod) % p;
+    }
+    *out = acc;
+    return 0;
+}
+
+/* ------------------------ O6: inclusion-exclusion over avoided positions */
+
+/* Sec. 2 (third approach): let the universe be every way of placing each
+ * pair k at two positions a, a+d_k of P, overlaps allowed, and A_i the
+ * placements that leave position i empty.  The sequences are the placements
+ * that leave no position empty, so by inclusion-exclusion their number
+ * (reflections distinct) is
+ *     sum over S subset of P of (-1)^{|S|} |A_S|,
+ * A_S being the placements that avoid every position of S.  A placement
+ * avoids S iff every pair lies inside T = P \ S, so |A_S| is the product over
+ * k of the number of pairs (a, a+d_k) with both ends in T.
+ * The sets T are enumerated through the positions of P in increasing order:
+ * "variable i" (0-based) is the i-th position of P, in T iff bit i of the
+ * enumerated word is set. */
+static void ie_positions(int span, const int *present, int *pos, int *np)
+{
+    int c = 0;
+    for (int i = 1; i <= span; i++) if (present[i]) pos[c++] = i;
+    *np = c;
+}
+
+/* prod_k #{a : a, a+d_k in T}, T given by in_t[1..span] (1 = in T). */
+static u128 ie_term(int n, int span, const int *d, const int *in_t)
+{
+    u128 prod = 1;
+    for (int k = 1; k <= n; k++) {
+        uint64_t pairs = 0;
+        for (int a = 1; a + d[k] <= span; a++) pairs += (uint64_t)(in_t[a] && in_t[a + d[k]]);
+        prod *= (u128)pairs;
+    }
+    return prod;
+}
+
+/* The count of sequences, reflections distinct, as out[0..1] (128 bits).
+ * Wrap-around 128-bit arithmetic gives the exact sum whenever the result
+ * is below 2^128, whatever the partial sums.  Limited to |P| <= 40. */
+int orc_ie_count(int variant, int n, uint64_t *out)
+{
+    int span, present[ORC_MAXSPAN + 1], d[ORC_MAXN + 1], pos[ORC_MAXSPAN], np;
+    if (orc_layout(variant, n, &span, present, d)) return -1;
+    ie_positions(span, present, pos, &np);
+    if (np > 40) return -1;
+    int in_t[ORC_MAXSPAN + 2];
+    u128 acc = 0;
+    for (uint64_t w = 0; w < ((uint64_t)1 << np); w++) {
+        memset(in_t, 0, sizeof(in_t));
+        int size_t_ = 0;
+        for (int i = 0; i < np; i++)
+            if ((w >> i) & 1) { in_t[pos[i]] = 1; size_t_++; }
+        u128 t = ie_term(n, span, d, in_t);
+        if ((np - size_t_) & 1) acc -= t;          /* (-1)^{|S|}, |S| = |P| - |T| */
+        else acc += t;
+    }
+    out[0] = (uint64_t)acc;
+    out[1] = (uint64_t)(acc >> 64);
+    return 0;
+}
+
+/* The same sum over one block of sets, modulo p: variables 0..m-1 run over
+ * both values, variable m+b is fixed to bit b of q.  Returns the block sum
+ * mod p in [0, p). */
+int orc_ie_partial_sum_mod(int variant, int n, int m, uint64_t q, uint64_t p, uint64_t *out)
+{
+    int span, present[ORC_MAXSPAN + 1], d[ORC_MAXN + 1], pos[ORC_MAXSPAN], np;
+    if (orc_layout(variant, n, &span, present, d)) return -1;
+    ie_positions(span, present, pos, &np);
+    if (m < 0 || m > np || m > 40 || p < 3 || p > ((uint64_t)1 << 62)) return -1;
+    if (np - m < 64 && (q >> (np - m)) != 0) return -1;
+    int in_t[ORC_MAXSPAN + 2];
+    uint64_t acc = 0;
+    for (uint64_t w = 0; w < ((uint64_t)1 << m); w++) {
+        memset(in_t, 0, sizeof(in_t));
+        int size_t_ = 0;
+        for (int i = 0; i < np; i++) {
+            int bit = (i < m) ? (int)((w >> i) & 1) : (int)((q >> (i - m)) & 1);
+            if (bit) { in_t[pos[i]] = 1; size_t_++; }
+        }
+        u128 t = ie_term(n, span, d, in_t);
+        uint64_t r = (uint64_t)(t % p);
+        if (((np - size_t_) & 1) && r) r = p - r;
+        acc = (acc + r) % p;
     }
     *out = acc;
     return 0;
