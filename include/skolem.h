@@ -56,7 +56,13 @@ enum {
  * A004075 / A176127 count both.  Lemma 2.1 yields the latter. */
 enum { SK_COUNT_REFLECTIONS_IDENTIFIED = 0, SK_COUNT_ALL = 1 };
 
-#define SK_MAX_N 28        /* largest n with a compiled exact kernel */
+/* Largest n with a compiled exact kernel.  The position set of every variant
+ * fits one 64-bit mask up to n = 31 (hooked Skolem spans 2n+1 = 63
+ * positions), and the three 62-bit moduli (M ~ 2^186) hold the signed sum
+ * C 2^{2n-1} with room to spare (|H| < 2^146 at n = 31).  Counting the
+ * 2^{2n-1} terms of n >= 26 takes GPU-days; the work-item calls below reach
+ * every order. */
+#define SK_MAX_N 31
 
 /* Arithmetic form of the term products (both give identical residues).
  * SK_ARITH_LIMBS: every term's product is formed exactly, as signed
@@ -80,7 +86,20 @@ enum { SK_ARITH_LIMBS = 0, SK_ARITH_MONTGOMERY = 1 };
  * Skolem, whose fixed position 2n+1 is odd) and 2^{2n-2} terms are summed;
  * the result (residues, coefficient) is the same.  Needs n >= 4; smaller
  * orders use SK_SYMMETRY_NEGATION (the report says which was used). */
-enum { SK_SYMMETRY_NEGATION = 0, SK_SYMMETRY_NEGATION_EVEN = 1 };
+/* SK_SYMMETRY_REVERSAL (Skolem and Langford; hooked Skolem: SK_EINVAL):
+ * Lemmas 2.2 and 2.3 -- the summand is unchanged under reversal
+ * i -> 2n+1-i, so of two assignments that are mirror images (with x_{2n}
+ * kept at +1: reversed if x_1 = +1, reversed and negated if x_1 = -1) one is
+ * summed twice and the other skipped; palindromic ones are summed once.  The
+ * walk runs over positions 2..h+1 and their mirror images; a work item fixes
+ * x_1 and the middle positions, and of each pair of mirror-image items one
+ * is evaluated with weight 2 (decided by the first 8 mirror pairs of the
+ * middle, from the outside in).  About (1/2 + 2^-9) of the 2^{2n-1} terms
+ * are evaluated; walk_bits (if given) must be even, at least twice the
+ * unrolled inner width and at most 2n-2.  The result is the same.  Needs
+ * n >= 6; smaller orders use SK_SYMMETRY_NEGATION (the report says which
+ * was used).  Exact-digit form only (arith = SK_ARITH_LIMBS). */
+enum { SK_SYMMETRY_NEGATION = 0, SK_SYMMETRY_NEGATION_EVEN = 1, SK_SYMMETRY_REVERSAL = 2 };
 #define SK_MAX_PRIMES 4
 
 typedef struct { uint64_t lo, hi; } sk_u128;   /* unsigned 128-bit integer */
@@ -378,6 +397,36 @@ int skolem_item_residues(int variant, int n, int m, uint64_t q_lo, uint64_t coun
 int sk_count_from_residues(int variant, int n, int convention, int nprimes,
                            const uint64_t *primes, uint64_t parts, const uint64_t *residues,
                            sk_u128 *out);
+
+/* ------------------------------------------ inclusion-exclusion count */
+
+/* Largest n with a compiled inclusion-exclusion kernel. */
+#define SK_MAX_IE_N 24
+
+/* The count by inclusion-exclusion over avoided positions -- the third
+ * counting approach of Sec. 2 (after Larsen) -- as an exact cross-check of
+ * skolem_count_ex that shares none of Lemma 2.1's arithmetic: with N_k(T)
+ * the number of pairs (a, a+d_k) inside T, the sequences (reflections
+ * distinct) number sum over T subset of P of (-1)^{|P|-|T|} prod_k N_k(T),
+ * 2^{2n} terms (no symmetry halves them), summed on the GPU as residues
+ * modulo the primes and rebuilt by the CRT (the result must lie in the lower
+ * half of the CRT range and agree with a fourth prime when one is given).
+ * Same arguments, output conventions and report as skolem_count_ex; opts
+ * (may be NULL) must keep arith = SK_ARITH_LIMBS and symmetry =
+ * SK_SYMMETRY_NEGATION (others: SK_EINVAL); checkpoints work as there (the
+ * method is part of the file's header).  1 <= n <= SK_MAX_IE_N. */
+int sk_count_inclusion_exclusion(int variant, int n, const sk_count_opts *opts, sk_u128 *out,
+                                 sk_count_report *rep);
+
+/* Residues of single work items of the inclusion-exclusion sum.  The 2n
+ * variables are the positions of P in increasing order (variable i is in T
+ * iff bit i of the set is 1); item q of walk width m fixes variables m..2n-1
+ * (bit b of q -> variable m+b) and runs variables 0..m-1 through all values;
+ * out (host, count x nprimes, row-major) receives each block sum modulo each
+ * prime.  q_lo + count <= 2^{2n-m}, count <= 2^20; primes as in
+ * skolem_item_residues. */
+int sk_ie_item_residues(int variant, int n, int m, uint64_t q_lo, uint64_t count, int nprimes,
+                        const uint64_t *primes, uint64_t *out);
 
 /* skolem_item_residues with a choice of arithmetic form (SK_ARITH_*). */
 int skolem_item_residues_ex(int variant, int n, int m, uint64_t q_lo, uint64_t count,

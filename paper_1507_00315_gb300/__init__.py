@@ -18,7 +18,9 @@ VARIANTS = {"skolem": SKOLEM, "langford": LANGFORD, "hooked": HOOKED}
 REFLECTIONS_IDENTIFIED, COUNT_ALL = 0, 1
 ARITH_LIMBS, ARITH_MONTGOMERY = 0, 1
 SYMMETRY_NEGATION, SYMMETRY_NEGATION_EVEN = 0, 1      # Lemma 2.2; Lemmas 2.2 + 2.4
-MAX_N = 28
+SYMMETRY_REVERSAL = 2                                  # Lemmas 2.2 + 2.3
+MAX_N = 31
+MAX_IE_N = 24
 MAX_PRIMES = 4
 NOALLOC_MAX_ITEMS = 16384
 
@@ -182,6 +184,13 @@ def lib():
         L.skolem_item_residues_noalloc.argtypes = [
             ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
             ctypes.POINTER(ctypes.c_uint64), ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]
+        L.sk_count_inclusion_exclusion.argtypes = [ctypes.c_int, ctypes.c_int,
+                                                   ctypes.POINTER(CountOpts),
+                                                   ctypes.POINTER(U128), ctypes.POINTER(CountReport)]
+        L.sk_ie_item_residues.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                          ctypes.c_uint64, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_uint64),
+                                          ctypes.POINTER(ctypes.c_uint64)]
         L.skolem_count_batch.argtypes = [ctypes.POINTER(Job), ctypes.c_int, ctypes.POINTER(BatchOpts),
                                          ctypes.POINTER(U128), ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(BatchReport)]
@@ -287,6 +296,32 @@ def count_ex(variant, n: int, **kw):
         raise SkolemError(st, f"skolem_count_ex({variant}, {n})")
     r = rep.as_dict()
     return (out.value() if r["complete"] else None), r
+
+
+def count_inclusion_exclusion(variant, n: int, **kw):
+    """sk_count_inclusion_exclusion: (count or None if incomplete, report
+    dict), the same keywords as count_ex (arith and symmetry left at their
+    defaults)."""
+    o = _opts(**kw)
+    out = U128()
+    rep = CountReport()
+    st = lib().sk_count_inclusion_exclusion(_variant(variant), n, ctypes.byref(o),
+                                            ctypes.byref(out), ctypes.byref(rep))
+    if st != SK_OK:
+        raise SkolemError(st, f"sk_count_inclusion_exclusion({variant}, {n})")
+    r = rep.as_dict()
+    return (out.value() if r["complete"] else None), r
+
+
+def ie_item_residues(variant, n: int, m: int, q_lo: int, count_: int, primes):
+    """sk_ie_item_residues: list of per-item lists of residues."""
+    k = len(primes)
+    P = (ctypes.c_uint64 * k)(*primes)
+    out = (ctypes.c_uint64 * (count_ * k))()
+    st = lib().sk_ie_item_residues(_variant(variant), n, m, q_lo, count_, k, P, out)
+    if st != SK_OK:
+        raise SkolemError(st, "sk_ie_item_residues")
+    return [list(out[i * k:(i + 1) * k]) for i in range(count_)]
 
 
 def count_plan(variant, n: int, **kw):

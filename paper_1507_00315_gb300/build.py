@@ -19,7 +19,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libskolem.so")
-MAX_N = 28
+MAX_N = 31
+MAX_IE_N = 24          # kMaxIeN of csrc/sk_ie.cuh: orders with an inclusion-exclusion kernel
+MIN_MIRROR_N = 6       # kMirrorMinN of csrc/sk_mirror.cuh: orders with a mirrored (Lemma 2.3) kernel
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Relocatable device code: the batch kernel calls the per-n walk functions
@@ -55,6 +57,10 @@ def _sources():
         p = os.path.join(gen, f"sk_exact_n{n:02d}.cu")
         text = (f'#include "sk_exact_launch.cuh"\n#include "sk_batch.cuh"\n'
                 f'SK_INSTANTIATE_EXACT({n})\nSK_DEFINE_BATCH({n})\n')
+        if n <= MAX_IE_N:
+            text += f'#include "sk_ie.cuh"\nSK_INSTANTIATE_IE({n})\n'
+        if n >= MIN_MIRROR_N:
+            text += f'#include "sk_mirror.cuh"\nSK_INSTANTIATE_MIRROR({n})\n'
         if not os.path.exists(p) or open(p).read() != text:
             with open(p, "w") as f:
                 f.write(text)

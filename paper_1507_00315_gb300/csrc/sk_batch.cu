@@ -27,6 +27,7 @@ SK_DECLARE_BATCH(13) SK_DECLARE_BATCH(14) SK_DECLARE_BATCH(15) SK_DECLARE_BATCH(
 SK_DECLARE_BATCH(17) SK_DECLARE_BATCH(18) SK_DECLARE_BATCH(19) SK_DECLARE_BATCH(20)
 SK_DECLARE_BATCH(21) SK_DECLARE_BATCH(22) SK_DECLARE_BATCH(23) SK_DECLARE_BATCH(24)
 SK_DECLARE_BATCH(25) SK_DECLARE_BATCH(26) SK_DECLARE_BATCH(27) SK_DECLARE_BATCH(28)
+SK_DECLARE_BATCH(29) SK_DECLARE_BATCH(30) SK_DECLARE_BATCH(31)
 
 namespace sk {
 
@@ -52,7 +53,7 @@ __device__ __forceinline__ Res4 batch_dispatch(int code, const BatchJobDev* j, c
     SK_BCASE(8) SK_BCASE(9) SK_BCASE(10) SK_BCASE(11) SK_BCASE(12) SK_BCASE(13) SK_BCASE(14)
     SK_BCASE(15) SK_BCASE(16) SK_BCASE(17) SK_BCASE(18) SK_BCASE(19) SK_BCASE(20)
     SK_BCASE(21) SK_BCASE(22) SK_BCASE(23) SK_BCASE(24) SK_BCASE(25) SK_BCASE(26)
-    SK_BCASE(27) SK_BCASE(28)
+    SK_BCASE(27) SK_BCASE(28) SK_BCASE(29) SK_BCASE(30) SK_BCASE(31)
     default: break;
   }
 #undef SK_BCASE

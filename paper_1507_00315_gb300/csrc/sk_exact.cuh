@@ -41,7 +41,7 @@
 
 namespace sk {
 
-constexpr int kMaxN = 28;        // largest n with a compiled kernel
+constexpr int kMaxN = 31;        // largest n with a compiled kernel (2n+1 <= 63 bits)
 constexpr int kMaxPrimes = 4;
 
 struct Prime {          // one modulus, split for the signed Montgomery step

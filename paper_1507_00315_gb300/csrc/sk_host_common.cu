@@ -76,6 +76,11 @@ uint64_t big_mod(const Big& a, uint64_t p) {
 }  // namespace
 
 int crt_coefficient(int n, int nprimes, const uint64_t* p, const uint64_t* H, sk_u128* coeff) {
+  return crt_shifted(2 * n - 1, nprimes, p, H, coeff);   // Lemma 2.1 divisor after Lemma 2.2
+}
+
+int crt_shifted(int s, int nprimes, const uint64_t* p, const uint64_t* H, sk_u128* coeff) {
+  if (s < 0 || s > 127) return SK_EINVAL;
   // Garner: x = r1 + p1 (t2 + p2 t3), 0 <= x < M = p1 p2 p3.
   const uint64_t r1 = H[0] % p[0], r2 = H[1] % p[1], r3 = H[2] % p[2];
   uint64_t t2 = mulmod((r2 + p[1] - r1 % p[1]) % p[1], invmod(p[0] % p[1], p[1]), p[1]);
@@ -84,11 +89,10 @@ int crt_coefficient(int n, int nprimes, const uint64_t* p, const uint64_t* H, sk
   u128 y = (u128)t2 + (u128)p[1] * t3;
   Big x = big_add(big_mul_u64(big_from_u128(y), p[0]), big_from_u128(r1));
   Big M = big_mul_u64(big_from_u128((u128)p[0] * p[1]), p[2]);
-  // H = C 2^{2n-1} >= 0, so x must lie in the lower half of [0, M).
+  // H = C 2^s >= 0, so x must lie in the lower half of [0, M).
   Big x2 = big_add(x, x);
   if (big_cmp(x2, M) >= 0) return SK_EMISMATCH;
   if (nprimes >= 4 && big_mod(x, p[3]) != H[3] % p[3]) return SK_EMISMATCH;
-  const int s = 2 * n - 1;              // Lemma 2.1 divisor after Lemma 2.2
   // low s bits must vanish
   for (int b = 0; b < s; ++b)
     if ((x.w[b / 64] >> (b % 64)) & 1ULL) return SK_EMISMATCH;

@@ -61,6 +61,9 @@ int prepare_primes(const sk_count_opts* o, int* nprimes, uint64_t* primes, Prime
 // division that yields the coefficient (pairings, reflections distinct).
 int crt_coefficient(int n, int nprimes, const uint64_t* primes, const uint64_t* H,
                     sk_u128* coeff);
+// The same with a divisor 2^shift (2n-1 for Lemma 2.1 after Lemma 2.2; 0 for
+// the inclusion-exclusion sum, which is the count itself).
+int crt_shifted(int shift, int nprimes, const uint64_t* primes, const uint64_t* H, sk_u128* out);
 
 uint32_t crc32(const void* data, size_t len);
 

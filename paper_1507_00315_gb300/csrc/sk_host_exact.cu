@@ -1,7 +1,10 @@
 // sk_host_exact.cu -- host runtime of the exact count: work planning (Sec.
 // 2.2: power-of-two splits of the assignments), launches, checkpointed
 // chunks, and the C ABI entry points skolem_count / skolem_count_ex /
-// skolem_item_residues.
+// skolem_item_residues, and the same runtime for the inclusion-exclusion
+// count (Sec. 2, third approach): sk_count_inclusion_exclusion /
+// sk_ie_item_residues.
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -12,6 +15,8 @@
 
 #include "sk_exact_launch.cuh"
 #include "sk_host_common.h"
+#include "sk_ie.cuh"
+#include "sk_mirror.cuh"
 
 namespace sk {
 
@@ -27,6 +32,7 @@ SK_EXTERN_EXACT(15) SK_EXTERN_EXACT(16) SK_EXTERN_EXACT(17) SK_EXTERN_EXACT(18)
 SK_EXTERN_EXACT(19) SK_EXTERN_EXACT(20) SK_EXTERN_EXACT(21) SK_EXTERN_EXACT(22)
 SK_EXTERN_EXACT(23) SK_EXTERN_EXACT(24) SK_EXTERN_EXACT(25) SK_EXTERN_EXACT(26)
 SK_EXTERN_EXACT(27) SK_EXTERN_EXACT(28)
+SK_EXTERN_EXACT(29) SK_EXTERN_EXACT(30) SK_EXTERN_EXACT(31)
 #undef SK_EXTERN_EXACT
 
 #define SK_EXTERN_LIMB(N)                                                          \
@@ -39,6 +45,7 @@ SK_EXTERN_LIMB(15) SK_EXTERN_LIMB(16) SK_EXTERN_LIMB(17) SK_EXTERN_LIMB(18)
 SK_EXTERN_LIMB(19) SK_EXTERN_LIMB(20) SK_EXTERN_LIMB(21) SK_EXTERN_LIMB(22)
 SK_EXTERN_LIMB(23) SK_EXTERN_LIMB(24) SK_EXTERN_LIMB(25) SK_EXTERN_LIMB(26)
 SK_EXTERN_LIMB(27) SK_EXTERN_LIMB(28)
+SK_EXTERN_LIMB(29) SK_EXTERN_LIMB(30) SK_EXTERN_LIMB(31)
 #undef SK_EXTERN_LIMB
 
 #define SK_ROW(N) {launch_exact<0, N, 3>, launch_exact<1, N, 3>}
@@ -47,7 +54,8 @@ static const ExactLaunchFn kTable[kMaxN + 1][2] = {
     SK_ROW(1), SK_ROW(2), SK_ROW(3), SK_ROW(4), SK_ROW(5), SK_ROW(6), SK_ROW(7),
     SK_ROW(8), SK_ROW(9), SK_ROW(10), SK_ROW(11), SK_ROW(12), SK_ROW(13), SK_ROW(14),
     SK_ROW(15), SK_ROW(16), SK_ROW(17), SK_ROW(18), SK_ROW(19), SK_ROW(20), SK_ROW(21),
-    SK_ROW(22), SK_ROW(23), SK_ROW(24), SK_ROW(25), SK_ROW(26), SK_ROW(27), SK_ROW(28)};
+    SK_ROW(22), SK_ROW(23), SK_ROW(24), SK_ROW(25), SK_ROW(26), SK_ROW(27), SK_ROW(28),
+    SK_ROW(29), SK_ROW(30), SK_ROW(31)};
 #undef SK_ROW
 
 ExactLaunchFn exact_launcher(int delta, int n, int nprimes) {
@@ -61,12 +69,66 @@ static const ExactLaunchFn kLimbTable[kMaxN + 1][2] = {
     SK_LROW(1), SK_LROW(2), SK_LROW(3), SK_LROW(4), SK_LROW(5), SK_LROW(6), SK_LROW(7),
     SK_LROW(8), SK_LROW(9), SK_LROW(10), SK_LROW(11), SK_LROW(12), SK_LROW(13), SK_LROW(14),
     SK_LROW(15), SK_LROW(16), SK_LROW(17), SK_LROW(18), SK_LROW(19), SK_LROW(20), SK_LROW(21),
-    SK_LROW(22), SK_LROW(23), SK_LROW(24), SK_LROW(25), SK_LROW(26), SK_LROW(27), SK_LROW(28)};
+    SK_LROW(22), SK_LROW(23), SK_LROW(24), SK_LROW(25), SK_LROW(26), SK_LROW(27), SK_LROW(28),
+    SK_LROW(29), SK_LROW(30), SK_LROW(31)};
 #undef SK_LROW
 
 ExactLaunchFn limb_launcher(int delta, int n) {
   if (delta < 0 || delta > 1 || n < 1 || n > kMaxN) return nullptr;
   return kLimbTable[n][delta];
+}
+
+#define SK_EXTERN_IE(N)                                                            \
+  extern template cudaError_t launch_ie<0, N>(const ExactLaunch&);                  \
+  extern template cudaError_t launch_ie<1, N>(const ExactLaunch&);
+SK_EXTERN_IE(1) SK_EXTERN_IE(2) SK_EXTERN_IE(3) SK_EXTERN_IE(4) SK_EXTERN_IE(5) SK_EXTERN_IE(6)
+SK_EXTERN_IE(7) SK_EXTERN_IE(8) SK_EXTERN_IE(9) SK_EXTERN_IE(10) SK_EXTERN_IE(11) SK_EXTERN_IE(12)
+SK_EXTERN_IE(13) SK_EXTERN_IE(14) SK_EXTERN_IE(15) SK_EXTERN_IE(16) SK_EXTERN_IE(17)
+SK_EXTERN_IE(18) SK_EXTERN_IE(19) SK_EXTERN_IE(20) SK_EXTERN_IE(21) SK_EXTERN_IE(22)
+SK_EXTERN_IE(23) SK_EXTERN_IE(24)
+#undef SK_EXTERN_IE
+
+#define SK_IROW(N) {launch_ie<0, N>, launch_ie<1, N>}
+static const ExactLaunchFn kIeTable[kMaxIeN + 1][2] = {
+    {nullptr, nullptr},
+    SK_IROW(1), SK_IROW(2), SK_IROW(3), SK_IROW(4), SK_IROW(5), SK_IROW(6), SK_IROW(7),
+    SK_IROW(8), SK_IROW(9), SK_IROW(10), SK_IROW(11), SK_IROW(12), SK_IROW(13), SK_IROW(14),
+    SK_IROW(15), SK_IROW(16), SK_IROW(17), SK_IROW(18), SK_IROW(19), SK_IROW(20), SK_IROW(21),
+    SK_IROW(22), SK_IROW(23), SK_IROW(24)};
+#undef SK_IROW
+static_assert(kMaxIeN == 24, "the table above lists n = 1..kMaxIeN");
+
+ExactLaunchFn ie_launcher(int delta, int n) {
+  if (delta < 0 || delta > 1 || n < 1 || n > kMaxIeN) return nullptr;
+  return kIeTable[n][delta];
+}
+
+#define SK_EXTERN_MIRROR(N)                                                        \
+  extern template cudaError_t launch_mirror<0, N>(const ExactLaunch&);              \
+  extern template cudaError_t launch_mirror<1, N>(const ExactLaunch&);
+SK_EXTERN_MIRROR(6) SK_EXTERN_MIRROR(7) SK_EXTERN_MIRROR(8) SK_EXTERN_MIRROR(9)
+SK_EXTERN_MIRROR(10) SK_EXTERN_MIRROR(11) SK_EXTERN_MIRROR(12) SK_EXTERN_MIRROR(13)
+SK_EXTERN_MIRROR(14) SK_EXTERN_MIRROR(15) SK_EXTERN_MIRROR(16) SK_EXTERN_MIRROR(17)
+SK_EXTERN_MIRROR(18) SK_EXTERN_MIRROR(19) SK_EXTERN_MIRROR(20) SK_EXTERN_MIRROR(21)
+SK_EXTERN_MIRROR(22) SK_EXTERN_MIRROR(23) SK_EXTERN_MIRROR(24) SK_EXTERN_MIRROR(25)
+SK_EXTERN_MIRROR(26) SK_EXTERN_MIRROR(27) SK_EXTERN_MIRROR(28) SK_EXTERN_MIRROR(29)
+SK_EXTERN_MIRROR(30) SK_EXTERN_MIRROR(31)
+#undef SK_EXTERN_MIRROR
+
+#define SK_MROW(N) {launch_mirror<0, N>, launch_mirror<1, N>}
+static const ExactLaunchFn kMirrorTable[kMaxN + 1][2] = {
+    {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr},
+    {nullptr, nullptr}, {nullptr, nullptr},
+    SK_MROW(6), SK_MROW(7), SK_MROW(8), SK_MROW(9), SK_MROW(10), SK_MROW(11), SK_MROW(12),
+    SK_MROW(13), SK_MROW(14), SK_MROW(15), SK_MROW(16), SK_MROW(17), SK_MROW(18), SK_MROW(19),
+    SK_MROW(20), SK_MROW(21), SK_MROW(22), SK_MROW(23), SK_MROW(24), SK_MROW(25), SK_MROW(26),
+    SK_MROW(27), SK_MROW(28), SK_MROW(29), SK_MROW(30), SK_MROW(31)};
+#undef SK_MROW
+static_assert(kMirrorMinN == 6 && kMaxN == 31, "the table above lists n = 6..31");
+
+ExactLaunchFn mirror_launcher(int delta, int n) {
+  if (delta < 0 || delta > 1 || n < kMirrorMinN || n > kMaxN) return nullptr;
+  return kMirrorTable[n][delta];
 }
 
 // Largest walk width of the exact form (compile-time table per (delta, n)).
@@ -77,7 +139,7 @@ static const int kLimbMaxM[kMaxN + 1][2] = {
     {0, 0}, SK_LM(1), SK_LM(2), SK_LM(3), SK_LM(4), SK_LM(5), SK_LM(6), SK_LM(7), SK_LM(8),
     SK_LM(9), SK_LM(10), SK_LM(11), SK_LM(12), SK_LM(13), SK_LM(14), SK_LM(15), SK_LM(16),
     SK_LM(17), SK_LM(18), SK_LM(19), SK_LM(20), SK_LM(21), SK_LM(22), SK_LM(23), SK_LM(24),
-    SK_LM(25), SK_LM(26), SK_LM(27), SK_LM(28)};
+    SK_LM(25), SK_LM(26), SK_LM(27), SK_LM(28), SK_LM(29), SK_LM(30), SK_LM(31)};
 #undef SK_LM
 
 // ------------------------------------------------------------ planning
@@ -103,7 +165,13 @@ int default_walk_bits(int n) {
   return m;
 }
 
+// What an exact count sums: Lemma 2.1's signed sum over the +-1 assignments
+// (after Lemma 2.2), or the inclusion-exclusion sum over the sets of
+// positions (Sec. 2, third approach; every one of the 2n variables free).
+enum { kMethodAlgebraic = 0, kMethodInclusionExclusion = 1 };
+
 struct Plan {
+  int method;
   int variant, n, delta, m, U, nprimes, block_threads, grid, arith;
   int symmetry;     // SK_SYMMETRY_* used
   int sign;         // Lemma 2.4 sign s (+1 / -1) when symmetry uses it
@@ -114,9 +182,18 @@ struct Plan {
   ExactLaunchFn fn;
 };
 
-static int make_plan(int variant, int n, const sk_count_opts* o, Plan* pl) {
+static int make_plan(int variant, int n, const sk_count_opts* o, Plan* pl,
+                     int method = kMethodAlgebraic) {
   if (variant < SK_SKOLEM || variant > SK_HOOKED || n < 1 || n > kMaxN) return SK_EINVAL;
   std::memset(pl, 0, sizeof(*pl));
+  pl->method = method;
+  if (method == kMethodInclusionExclusion) {
+    // the same walk over all 2n variables of P: no symmetry, exact-digit form
+    if (n > kMaxIeN) return SK_EINVAL;
+    if (o && (o->arith != SK_ARITH_LIMBS || o->symmetry != SK_SYMMETRY_NEGATION)) return SK_EINVAL;
+  } else if (method != kMethodAlgebraic) {
+    return SK_EINVAL;
+  }
   pl->variant = variant;
   pl->n = n;
   pl->delta = (variant == SK_LANGFORD) ? 1 : 0;
@@ -141,7 +218,11 @@ static int make_plan(int variant, int n, const sk_count_opts* o, Plan* pl) {
   // variable -- the highest of that parity -- is held at +1 and the sum
   // doubled; with s = -1 the sum is 0.
   const int sym = o ? o->symmetry : SK_SYMMETRY_NEGATION;
-  if (sym != SK_SYMMETRY_NEGATION && sym != SK_SYMMETRY_NEGATION_EVEN) return SK_EINVAL;
+  if (sym != SK_SYMMETRY_NEGATION && sym != SK_SYMMETRY_NEGATION_EVEN &&
+      sym != SK_SYMMETRY_REVERSAL)
+    return SK_EINVAL;
+  if (sym == SK_SYMMETRY_REVERSAL && (variant == SK_HOOKED || pl->arith != SK_ARITH_LIMBS))
+    return SK_EINVAL;                     // hooked Skolem's P is not reversal-symmetric
   pl->symmetry = SK_SYMMETRY_NEGATION;
   pl->sign = 1;
   pl->fixed_bit = 0;
@@ -159,12 +240,31 @@ static int make_plan(int variant, int n, const sk_count_opts* o, Plan* pl) {
     if (pl->m > pl->fixed_bit) return SK_EINVAL;        // the fixed bit must lie above the walk
   }
   if (pl->m < pl->U || pl->m > F || pl->m > mmax || F - pl->m > 56) return SK_EINVAL;
+  if (method == kMethodInclusionExclusion) Feff = F + 1;   // max P is a variable too
   pl->items = 1ULL << (Feff - pl->m);
+  // Lemma 2.3 (reversal): the mirrored walk over bits 1..h and their mirror
+  // images, items = x_1 and the middle bits, one of each pair of mirror-image
+  // items enumerated with weight 2 (sk_mirror.cuh)
+  if (sym == SK_SYMMETRY_REVERSAL && n >= kMirrorMinN) {
+    int m = pl->m;
+    if (!(o && o->walk_bits)) {
+      const int cap = std::min(mmax, 2 * n - 2) & ~1;
+      m = (m + 1) & ~1;
+      if (m > cap) m = cap;
+      if (m < 2 * pl->U) m = 2 * pl->U;
+    }
+    if ((m & 1) || m / 2 < pl->U || m > 2 * n - 2 || m > mmax) return SK_EINVAL;
+    pl->m = m;
+    pl->symmetry = SK_SYMMETRY_REVERSAL;
+    pl->items = 2 * mirror_shape(n, m / 2).per_side;
+  }
   pl->block_threads = (o && o->block_threads) ? o->block_threads : 256;
   if (pl->block_threads < 32 || pl->block_threads > 256 || (pl->block_threads & 31)) return SK_EINVAL;
   pl->grid = (o && o->grid > 0) ? o->grid : 0;
-  pl->fn = pl->arith == SK_ARITH_LIMBS ? limb_launcher(pl->delta, n)
-                                       : exact_launcher(pl->delta, n, pl->nprimes);
+  pl->fn = method == kMethodInclusionExclusion     ? ie_launcher(pl->delta, n)
+           : pl->symmetry == SK_SYMMETRY_REVERSAL ? mirror_launcher(pl->delta, n)
+           : pl->arith == SK_ARITH_LIMBS          ? limb_launcher(pl->delta, n)
+                                                  : exact_launcher(pl->delta, n, pl->nprimes);
   if (!pl->fn) return SK_EINVAL;
   return SK_OK;
 }
@@ -241,6 +341,8 @@ static std::string ckpt_header(const Plan& pl, unsigned long long chunk_items,
                 nchunks);
   std::string h(buf);
   if (pl.symmetry == SK_SYMMETRY_NEGATION_EVEN) h += " s=lemma2.4";
+  if (pl.symmetry == SK_SYMMETRY_REVERSAL) h += " s=lemma2.3";
+  if (pl.method == kMethodInclusionExclusion) h += " method=inclusion-exclusion";
   return h;
 }
 
@@ -394,10 +496,11 @@ int finalize_count(int variant, int n, int convention, int nprimes, const uint64
   return apply_convention(variant, n, convention, coeff, out);
 }
 
-int count_impl(int variant, int n, const sk_count_opts* o, sk_u128* out, sk_count_report* rep) {
+int count_impl(int variant, int n, const sk_count_opts* o, sk_u128* out, sk_count_report* rep,
+               int method = kMethodAlgebraic) {
   auto t0 = std::chrono::steady_clock::now();
   Plan pl;
-  int st = make_plan(variant, n, o, &pl);
+  int st = make_plan(variant, n, o, &pl, method);
   if (st) return st;
   if (o && o->convention != SK_COUNT_REFLECTIONS_IDENTIFIED && o->convention != SK_COUNT_ALL)
     return SK_EINVAL;
@@ -491,7 +594,9 @@ int count_impl(int variant, int n, const sk_count_opts* o, sk_u128* out, sk_coun
     for (int i = 0; i < pl.nprimes; ++i) H[i] = (H[i] * 2) % pl.primes[i];
   sk_u128 coeff = {0, 0};
   if (complete) {
-    st = crt_coefficient(n, pl.nprimes, pl.primes, H, &coeff);
+    // Lemma 2.1: H = C 2^{2n-1}; inclusion-exclusion: H = C
+    st = crt_shifted(method == kMethodInclusionExclusion ? 0 : 2 * n - 1, pl.nprimes, pl.primes, H,
+                     &coeff);
     if (st) return st;
   }
   if (rep) {
@@ -526,7 +631,8 @@ int count_impl(int variant, int n, const sk_count_opts* o, sk_u128* out, sk_coun
 }
 
 int item_residues_impl(int variant, int n, int m, uint64_t q_lo, uint64_t count, int nprimes,
-                       const uint64_t* primes, int arith, uint64_t* out) {
+                       const uint64_t* primes, int arith, uint64_t* out,
+                       int method = kMethodAlgebraic) {
   if (!out || !primes || count == 0 || count > (1ULL << 20)) return SK_EINVAL;
   sk_count_opts o;
   std::memset(&o, 0, sizeof(o));
@@ -535,7 +641,7 @@ int item_residues_impl(int variant, int n, int m, uint64_t q_lo, uint64_t count,
   for (int i = 0; i < nprimes && i < SK_MAX_PRIMES; ++i) o.primes[i] = primes[i];
   o.walk_bits = m;
   Plan pl;
-  int st = make_plan(variant, n, &o, &pl);
+  int st = make_plan(variant, n, &o, &pl, method);
   if (st) return st;
   if (q_lo >= pl.items || count > pl.items - q_lo) return SK_EINVAL;
   st = check_device();
@@ -630,4 +736,15 @@ extern "C" int skolem_item_residues_ex(int variant, int n, int m, uint64_t q_lo,
                                        int nprimes, const uint64_t* primes, int arith,
                                        uint64_t* out) {
   return sk::item_residues_impl(variant, n, m, q_lo, count, nprimes, primes, arith, out);
+}
+
+extern "C" int sk_count_inclusion_exclusion(int variant, int n, const sk_count_opts* opts,
+                                            sk_u128* out, sk_count_report* rep) {
+  return sk::count_impl(variant, n, opts, out, rep, sk::kMethodInclusionExclusion);
+}
+
+extern "C" int sk_ie_item_residues(int variant, int n, int m, uint64_t q_lo, uint64_t count,
+                                   int nprimes, const uint64_t* primes, uint64_t* out) {
+  return sk::item_residues_impl(variant, n, m, q_lo, count, nprimes, primes, SK_ARITH_LIMBS, out,
+                                sk::kMethodInclusionExclusion);
 }

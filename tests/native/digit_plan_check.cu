@@ -1,5 +1,5 @@
 // Host check of the exact kernel's per-term digit product for every
-// (delta, n) plan the library compiles (n = 1..28, Skolem / hooked and
+// (delta, n) plan the library compiles (n = 1..31, Skolem / hooked and
 // Langford distances):
 //   * (-1)^NEG prod_k c_k == T * sum_i r_i 2^{31 i}, compared modulo two primes;
 //   * every digit below the top lies in [0, 2^31);

@@ -12,7 +12,7 @@ import paper_1507_00315_gb300 as sk
 
 @pytest.mark.parametrize("variant,n,kw", [
     (3, 8, {}),                                     # no such variant
-    (0, 0, {}), (0, 29, {}),                        # orders without a compiled kernel
+    (0, 0, {}), (0, 32, {}),                        # orders without a compiled kernel
     (0, 12, {"nprimes": 2}), (0, 12, {"nprimes": 5}),
     (0, 12, {"nprimes": 4, "primes": [4, 0, 0, 0]}),            # an even modulus
     (0, 12, {"nprimes": 3, "primes": [(1 << 62) + 1, 0, 0]}),   # above 2^62
@@ -61,3 +61,31 @@ def test_pt_estimate_arguments(variant, n, budget, kw):
     with pytest.raises(sk.SkolemError) as e:
         sk.pt_estimate(variant, n, budget, **kw)
     assert e.value.status == sk.SK_EINVAL
+
+
+def test_inclusion_exclusion_refusals_before_device_work():
+    # orders beyond the compiled inclusion-exclusion kernels, and options the
+    # method does not have (no symmetry halves it; exact-digit form only)
+    for args, kw in (((0, sk.MAX_IE_N + 1), {}), ((0, 0), {}), ((3, 8), {}),
+                     ((0, 12), {"arith": sk.ARITH_MONTGOMERY}),
+                     ((0, 12), {"symmetry": sk.SYMMETRY_NEGATION_EVEN}),
+                     ((0, 12), {"walk_bits": 2}), ((0, 12), {"nprimes": 2})):
+        with pytest.raises(sk.SkolemError) as e:
+            sk.count_inclusion_exclusion(*args, **kw)
+        assert e.value.status == sk.SK_EINVAL, (args, kw)
+    with pytest.raises(sk.SkolemError) as e:
+        sk.ie_item_residues(0, 12, 9, 1 << 15, 1, sk.default_primes()[:3])   # beyond 2^{2n-m} items
+    assert e.value.status == sk.SK_EINVAL
+
+
+def test_reversal_refusals_before_device_work():
+    # Lemma 2.3 needs a reversal-symmetric P (not hooked Skolem), the exact
+    # digit form, and an even walk width 2h with U <= h <= n-1
+    U = sk.count_plan(0, 14)["inner_bits"]
+    for args, kw in (((2, 12), {}), ((0, 12), {"arith": sk.ARITH_MONTGOMERY}),
+                     ((0, 14), {"walk_bits": 2 * U + 1}), ((0, 14), {"walk_bits": 2 * U - 2}),
+                     ((0, 14), {"walk_bits": 28})):
+        with pytest.raises(sk.SkolemError) as e:
+            sk.count_plan(*args, symmetry=sk.SYMMETRY_REVERSAL, **kw)
+        assert e.value.status == sk.SK_EINVAL, (args, kw)
+

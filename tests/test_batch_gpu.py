@@ -50,6 +50,6 @@ def test_autotune_then_batch():
 
 def test_batch_invalid():
     with pytest.raises(sk.SkolemError):
-        sk.count_batch([(0, 30)])
+        sk.count_batch([(0, sk.MAX_N + 1)])      # beyond the compiled orders
     with pytest.raises(sk.SkolemError):
         sk.count_batch([])

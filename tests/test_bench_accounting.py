@@ -18,7 +18,7 @@ def test_operations_per_term():
     assert bench.alg_ops_per_term(0, 24) == 67
     # one cumulative bound-product length per int32 group, growing group by group
     for delta in (0, 1):
-        for n in range(4, 29):
+        for n in range(4, 32):
             bits = bench.group_bits(delta, n)
             assert len(bits) == bench.groups(delta, n)
             assert bits == sorted(bits) and bits[-1] >= bits[0]

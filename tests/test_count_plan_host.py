@@ -11,7 +11,7 @@ NEG_EVEN = sk.SYMMETRY_NEGATION_EVEN
 
 
 @pytest.mark.parametrize("variant", [0, 1, 2])
-@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 8, 12, 16, 20, 21, 24, 28])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 8, 12, 16, 20, 21, 24, 28, 29, 30, 31])
 def test_plan_covers_the_half_sum(variant, n):
     r = sk.count_plan(variant, n)
     assert r["terms"] == 2 ** (2 * n - 1)                    # Lemma 2.2: x at max P fixed
@@ -51,8 +51,28 @@ def test_checkpoint_chunks():
 
 
 def test_plan_argument_checks():
-    for args, kw in (((3, 8), {}), ((0, 29), {}), ((0, 12), {"walk_bits": 2}),
+    for args, kw in (((3, 8), {}), ((0, 32), {}), ((0, 12), {"walk_bits": 2}),
                      ((0, 12), {"convention": 3}), ((0, 12), {"nprimes": 2})):
         with pytest.raises(sk.SkolemError) as e:
             sk.count_plan(*args, **kw)
         assert e.value.status == sk.SK_EINVAL
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("n", [6, 8, 12, 16, 20, 24, 28, 31])
+def test_reversal_plan(variant, n):
+    # Lemma 2.3: x_1 and the middle positions fixed per item, an even walk
+    # width; one of each mirror-image pair of items (decided by up to 8
+    # mirror pairs of the middle), so the items are (1/2 + 2^-(depth+1)) of
+    # the 2^{2n-1-m} of the plain half-sum (depth = min(8, middle pairs))
+    r = sk.count_plan(variant, n, symmetry=sk.SYMMETRY_REVERSAL)
+    m = r["walk_bits"]
+    assert r["symmetry"] == sk.SYMMETRY_REVERSAL and m % 2 == 0
+    assert r["inner_bits"] <= m // 2 <= n - 1
+    pairs = n - 1 - m // 2
+    depth = min(8, pairs)
+    per_side = sum(2 ** (d + 2 * (pairs - 1 - d)) for d in range(depth)) + \
+        2 ** (depth + 2 * (pairs - depth))
+    assert r["items"] == 2 * per_side
+    assert r["terms"] == r["items"] << m
+    assert r["items"] * 2 ** m <= 2 ** (2 * n - 1) * (0.5 + 2.0 ** -(depth + 1)) + 1

@@ -28,4 +28,4 @@ def test_every_digit_plan_on_the_host():
     lines = r.stdout.strip().splitlines()
     assert lines[-1] == "total bad=0", "\n".join(l for l in lines if not l.endswith("bad=0"))
     assert r.returncode == 0
-    assert len(lines) == 2 * 28 + 1
+    assert len(lines) == 2 * 31 + 1

@@ -105,7 +105,8 @@ def test_item_residues_ragged_tiles(variant):
 
 
 @pytest.mark.parametrize("variant,n,m", [(SK, 24, 9), (LA, 24, 9), (HO, 26, 8), (SK, 28, 7),
-                                         (LA, 28, 7), (HO, 21, 10)])
+                                         (LA, 28, 7), (HO, 21, 10), (SK, 29, 7), (LA, 30, 7),
+                                         (HO, 31, 7), (SK, 31, 6), (LA, 31, 7)])
 def test_large_orders_items_both_forms(variant, n, m):
     # the widest limb accumulators and the longest Montgomery chains, on
     # items small enough for the oracle (prefixes spread over the range)
@@ -136,7 +137,7 @@ def test_custom_primes_and_check_prime():
 
 
 def test_invalid_arguments():
-    for bad in ((3, 4), (SK, 0), (SK, 29), (-1, 5)):
+    for bad in ((3, 4), (SK, 0), (SK, 32), (-1, 5)):
         with pytest.raises(sk.SkolemError) as e:
             sk.count(*bad)
         assert e.value.status == sk.SK_EINVAL
@@ -224,10 +225,10 @@ def test_lemma_2_4_checkpoint(tmp_path):
 @pytest.mark.parametrize("variant", [SK, LA, HO])
 def test_every_order_one_item_vs_oracle(variant):
     # Each (delta, n) kernel has its own compile-time plan (grouping, tail or
-    # digit form, product shape): one work item of every order 4..28, both
+    # digit form, product shape): one work item of every order 4..31, both
     # arithmetic forms, against the oracle's block sum.
     primes = sk.default_primes()[:4]
-    for n in range(4, 29):
+    for n in range(4, 32):
         F = 2 * n - 1
         m = min(9, F)
         q = (0x2D5A3C6B9E1F4 * (n + 7)) % (1 << (F - m))

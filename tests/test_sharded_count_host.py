@@ -102,3 +102,28 @@ def test_two_ranks_combine_their_shares():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert res[0] == res[1] == oracle.backtrack_count(1, 8)                 # 300 (Table 8: 150)
+
+
+@pytest.mark.parametrize("variant,n", [(0, 24), (0, 25), (0, 28), (0, 29), (1, 27), (1, 28)])
+def test_crt_range_at_the_largest_printed_orders(variant, n, skolem_table, langford_table):
+    # The host step at the largest orders the paper counts exactly (Tables 7
+    # and 8, up to S(29) and L(28)): the signed sum of Lemma 2.1 after
+    # Lemma 2.2 is H = 2 C 2^{2n-1} (C the printed count, reflections
+    # identified), |H| < 2^{135} at S(29), far inside the three moduli's
+    # range M ~ 2^{186}.  Its residues, as one part, must rebuild C exactly
+    # (the 2n-1 low bits vanish, the quotient is the count), a fourth
+    # modulus must agree, and a residue off by one modulo any prime must be
+    # caught.
+    C = (skolem_table if variant == 0 else langford_table)[n]
+    H = 2 * C << (2 * n - 1)
+    assert H < 1 << 135
+    res = [H % p for p in PRIMES]
+    assert sk.count_from_residues(variant, n, [res], PRIMES) == C
+    assert sk.count_from_residues(variant, n, [res[:3]], PRIMES[:3]) == C
+    assert sk.count_from_residues(variant, n, [res], PRIMES, sk.COUNT_ALL) == 2 * C
+    for i in range(4):
+        bad = list(res)
+        bad[i] = (bad[i] + 1) % PRIMES[i]
+        with pytest.raises(sk.SkolemError) as e:
+            sk.count_from_residues(variant, n, [bad], PRIMES)
+        assert e.value.status == sk.SK_EMISMATCH
