@@ -249,47 +249,202 @@ def run_extra(args, world, rank, local):
     torch.cuda.set_device(local)
     sh = torch.cuda.current_stream().cuda_stream
     if args.config == "batch":
-        jobs = [(v, n) for v in (0, 1, 2) for n in range(4, args.nmax + 1)]
-        out = {}
-        counts = None
-        for name, kw in (("per_job", {"mode": sk.BATCH_PER_JOB}), ("persistent_graph", {}),
-                         ("persistent_graph_autotuned", {"autotune": True})):
-            c, st, rep = sk.count_batch(jobs, repeats=max(1, args.steps), stream=sh, **kw)
-            assert counts is None or c == counts
-            counts = c
-            out[name] = {"kernel_ms_min": rep["kernel_ms_min"], "launches": rep["launches"],
-                         "terms_per_s": rep["terms"] / (rep["kernel_ms_min"] / 1e3),
-                         "block_threads": rep["block_threads"], "grid": rep["grid"],
-                         "wall_ms": rep["wall_ms"]}
-        line = {"metric": "batched sweep terms/s, persistent graph launch vs one launch per job",
-                "config": {"workload": f"{{Skolem, Langford, hooked}} x n=4..{args.nmax}, 3 moduli",
-                           "jobs": len(jobs)},
-                "unit": "terms/s", "results": out,
-                "speedup_persistent_vs_per_job": out["per_job"]["kernel_ms_min"] /
-                out["persistent_graph"]["kernel_ms_min"]}
+        line = run_batch_bench(args, sk, sh)
+    elif args.config == "slices":
+        line = run_slices_bench(args, sk, sh)
+    elif args.config == "ie":
+        line = run_ie_bench(args, sk, sh)
+    elif args.config == "symmetry":
+        line = run_symmetry_bench(args, sk, sh)
     elif args.config == "pt":
         line = run_pt_bench(args, sk, sh)
     elif args.config == "pt-large":
         line = run_pt_large_bench(args, sk, sh)
+    elif args.config == "pt-bias":
+        line = run_pt_bias_bench(args, sk, sh)
+    elif args.config == "pt-gain":
+        line = run_pt_gain_bench(args, sk, sh)
     else:
         import tempfile
         res = {}
-        for sym in (sk.SYMMETRY_NEGATION, sk.SYMMETRY_NEGATION_EVEN):
+        names = {sk.SYMMETRY_NEGATION: "", sk.SYMMETRY_NEGATION_EVEN: " lemma 2.4",
+                 sk.SYMMETRY_REVERSAL: " lemma 2.3"}
+        want = {(0, 24): EXACT_S[24], (1, 24): EXACT_L[24]}
+        for sym in args.symmetries:
             for v, n in ((0, 24), (1, 24)):
                 path = os.path.join(args.ckpt_dir or tempfile.gettempdir(),
                                     f"sk_ckpt_{v}_{n}_s{sym}.txt")
                 c, rep = sk.count_ex(v, n, nprimes=4, checkpoint=path, stream=sh, symmetry=sym)
-                key = f"{'SL'[v]}({n})" + (" lemma 2.4" if sym else "")
-                res[key] = {"count": str(c), "kernel_s": rep["kernel_ms"] / 1e3,
+                key = f"{'SL'[v]}({n})" + names[sym]
+                res[key] = {"count": str(c), "equals_paper": c == want[(v, n)],
+                            "kernel_s": rep["kernel_ms"] / 1e3,
                             "wall_s": rep["wall_ms"] / 1e3, "chunks": rep["chunks_total"],
                             "resumed": rep["chunks_resumed"], "terms": rep["terms"],
+                            "walk_bits": rep["walk_bits"],
                             "terms_per_s": rep["terms"] / max(rep["kernel_ms"], 1e-9) * 1e3}
         line = {"metric": "exact S(24), L(24): terms/s, checkpointed, 4 moduli",
-                "config": {"workload": "S(24), L(24), 2^47 terms each (Lemma 2.2), 3 moduli + "
-                                       "check modulus; again with Lemma 2.4 (2^46 terms each)"},
+                "config": {"workload": "S(24), L(24): 2^47 terms each with Lemma 2.2 alone, 2^46 "
+                                       "with Lemma 2.4, (1/2 + 2^-9) 2^47 with Lemma 2.3; 3 moduli + "
+                                       "check modulus",
+                           "symmetries": [names[s].strip() or "lemma 2.2" for s in args.symmetries]},
                 "unit": "terms/s", "results": res}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_batch_bench(args, sk, sh):
+    """The batched sweep: {Skolem, Langford, hooked} x n = 4..nmax, 3 moduli,
+    as one persistent graph-captured launch and as one launch per job
+    (largest job first, same stream), each timed over `steps` (at least 5)
+    separate calls after one warm-up call, reported as median, minimum and
+    maximum of the device time between events around the whole sweep; the
+    autotuned persistent run (walk width and block size per job) beside them.
+    Every mode must give the same counts."""
+    import statistics as stt
+    jobs = [(v, n) for v in (0, 1, 2) for n in range(4, args.nmax + 1)]
+    reps = max(5, args.steps)
+    modes = [("per_job", {"mode": sk.BATCH_PER_JOB}), ("persistent_graph", {})]
+    if not args.no_autotune:
+        modes.append(("persistent_graph_autotuned", {"autotune": True}))
+    out, counts = {}, None
+    for name, kw in modes:
+        times, rep = [], None
+        for i in range(reps + 1):
+            c, st, rep = sk.count_batch(jobs, repeats=1, stream=sh, **kw)
+            assert counts is None or c == counts, name
+            counts = c
+            if i:                                   # the first call warms up
+                times.append(rep["kernel_ms"])
+        med = stt.median(times)
+        out[name] = {"kernel_ms_median": med, "kernel_ms_min": min(times),
+                     "kernel_ms_max": max(times), "repeats": reps,
+                     "spread_frac": (max(times) - min(times)) / med,
+                     "terms_per_s_median": rep["terms"] / (med / 1e3), "launches": rep["launches"],
+                     "block_threads": rep["block_threads"], "grid": rep["grid"]}
+    pj, pg = out["per_job"], out["persistent_graph"]
+    return {"metric": "batched sweep terms/s, persistent graph launch vs one launch per job",
+            "config": {"workload": f"{{Skolem, Langford, hooked}} x n=4..{args.nmax}, 3 moduli",
+                       "jobs": len(jobs), "terms": sum(1 << (2 * n - 1) for _, n in jobs)},
+            "unit": "terms/s", "results": out,
+            "speedup_persistent_vs_per_job_median": pj["kernel_ms_median"] / pg["kernel_ms_median"],
+            # beyond the spread: the slowest persistent run beats the fastest per-job run
+            "persistent_beats_per_job_beyond_spread": pg["kernel_ms_max"] < pj["kernel_ms_min"]}
+
+
+def run_symmetry_bench(args, sk, sh):
+    """What the extra symmetries buy on the mid-size workload: every job with
+    Lemma 2.2 alone (2^{2n-1} terms), with Lemma 2.4 on top (half of them,
+    in the existence classes; none outside) and with Lemma 2.3 on top (the
+    mirrored walk, about half), best of `steps` runs each.  The counts must
+    agree.  Reported per job: kernel time, terms evaluated, and the
+    equivalent rate 2^{2n-1} / time (the plain half-sum's terms per second of
+    the run that skips some of them)."""
+    modes = (("lemma_2_2", sk.SYMMETRY_NEGATION), ("lemma_2_4", sk.SYMMETRY_NEGATION_EVEN),
+             ("lemma_2_3", sk.SYMMETRY_REVERSAL))
+    out, tot = {}, {name: 0.0 for name, _ in modes}
+    for v, n in JOBS:
+        row, c0 = {}, None
+        for name, sym in modes:
+            best = None
+            for _ in range(max(1, args.steps)):
+                c, rep = sk.count_ex(v, n, stream=sh, symmetry=sym)
+                assert c0 is None or c == c0, (v, n, name)
+                c0 = c
+                best = rep["kernel_ms"] if best is None else min(best, rep["kernel_ms"])
+            row[name] = {"kernel_ms": best, "terms_evaluated": rep["terms"],
+                         "walk_bits": rep["walk_bits"], "symmetry_used": rep["symmetry"],
+                         "equivalent_terms_per_s": (1 << (2 * n - 1)) / max(best, 1e-9) * 1e3}
+            tot[name] += best
+        out[f"{'SL'[v]}({n})"] = row
+    return {"metric": "exact count time with Lemma 2.2 alone, + Lemma 2.4, + Lemma 2.3",
+            "unit": "ms", "config": {"workload": WORKLOAD},
+            "results": out, "total_kernel_ms": tot,
+            "speedup_vs_lemma_2_2": {k: tot["lemma_2_2"] / v for k, v in tot.items() if v > 0}}
+
+
+def run_ie_bench(args, sk, sh):
+    """The inclusion-exclusion count (Sec. 2, third approach) beside the
+    algebraic count of Lemma 2.1 on the mid-size workload: each job counted
+    both ways (the counts must agree bit for bit), best of `steps` runs of
+    each.  Inclusion-exclusion sums 2^{2n} terms, the algebraic count 2^{2n-1}
+    (Lemma 2.2); both walks do the same work per term (n correlation updates,
+    the exact product, one signed accumulate)."""
+    peak = sk.int32_peak(1)[0]
+    out = {}
+    for v, n in JOBS:
+        row = {}
+        for name, fn in (("algebraic", sk.count_ex), ("inclusion_exclusion",
+                                                      sk.count_inclusion_exclusion)):
+            best, c0 = None, None
+            for _ in range(max(1, args.steps)):
+                c, rep = fn(v, n, stream=sh)
+                assert c0 is None or c == c0
+                c0 = c
+                best = rep["kernel_ms"] if best is None else min(best, rep["kernel_ms"])
+            rate = rep["terms"] / (best / 1e3)
+            row[name] = {"count": str(c0), "terms": rep["terms"], "kernel_ms": best,
+                         "terms_per_s": rate,
+                         "int32_frac": alg_ops_per_term(v, n) * rate / peak}
+        assert row["algebraic"]["count"] == row["inclusion_exclusion"]["count"], (v, n, row)
+        row["time_ratio_ie_vs_algebraic"] = (row["inclusion_exclusion"]["kernel_ms"] /
+                                             row["algebraic"]["kernel_ms"])
+        out[f"{'SL'[v]}({n})"] = row
+    return {"metric": "exact count terms/s: inclusion-exclusion vs the algebraic method",
+            "unit": "terms/s",
+            "config": {"workload": WORKLOAD.replace("one launch per job", "each job both ways"),
+                       "int32_peak_tops": peak / 1e12,
+                       "peak_source": "measured: sk_int32_peak mode 1, same run"},
+            "results": out}
+
+
+SLICE_CASES = [(0, 21), (1, 23), (0, 24), (1, 24), (0, 25), (1, 27), (0, 28), (1, 28), (0, 29),
+               (2, 30), (1, 31)]
+
+
+def run_slices_bench(args, sk, sh):
+    """Timed slices of the large exact counts: the first 2^slice_bits terms
+    (one checkpoint chunk) of S(21) .. S(29), L(23) .. L(31) and hooked
+    Skolem n = 30, four moduli, Lemma 2.4 on where it applies, with the
+    plan the library picks for the whole count.  A full count's time is
+    projected from the slice's rate (every work item walks the same Gray
+    schedule, so the rate does not depend on which items are timed)."""
+    import tempfile
+    peak = sk.int32_peak(1)[0]
+    out = {}
+    d = args.ckpt_dir or tempfile.mkdtemp(prefix="sk_slices_")
+    for v, n in SLICE_CASES[:args.pt_cases + 2]:
+        sym = sk.SYMMETRY_NEGATION_EVEN
+        path = os.path.join(d, f"slice_{v}_{n}.ckpt")
+        if os.path.exists(path):
+            os.remove(path)
+        plan = sk.count_plan(v, n, nprimes=4, checkpoint=path, symmetry=sym)
+        m = plan["walk_bits"]
+        chunk = 1 << max(0, args.slice_bits - m)
+        best = None
+        for rep_i in range(2):                  # first call warms the kernel up
+            if os.path.exists(path):
+                os.remove(path)
+            c, rep = sk.count_ex(v, n, nprimes=4, checkpoint=path, chunk_items=chunk,
+                                 max_chunks=1, symmetry=sym, stream=sh)
+            # one chunk; a slice as large as the count is the whole count
+            assert rep["chunks_done"] == 1 and (c is None) == (rep["chunks_total"] > 1), rep
+            best = rep["kernel_ms"] if best is None else min(best, rep["kernel_ms"])
+        os.remove(path)
+        terms = chunk << m
+        rate = terms / (best / 1e3)
+        ops = alg_ops_per_term(v, n)
+        out[f"{'SLH'[v]}({n})"] = {
+            "terms_total": plan["terms"], "walk_bits": m, "items_total": plan["items"],
+            "slice_terms": terms, "slice_ms": best, "terms_per_s": rate,
+            "ops_per_term": ops, "int32_frac": ops * rate / peak,
+            "projected_hours_full_count": plan["terms"] / rate / 3600.0}
+    return {"metric": "exact count slices beyond the mid-size workload: terms/s and projected time",
+            "unit": "terms/s",
+            "config": {"workload": f"first 2^{args.slice_bits} terms of each count, 4 moduli, "
+                                   "Lemma 2.2 + 2.4, the planner's walk width",
+                       "int32_peak_tops": peak / 1e12,
+                       "peak_source": "measured: sk_int32_peak mode 1, same run"},
+            "results": out}
 
 
 # 32-bit integer operations of one Metropolis iteration of one chain in
@@ -392,6 +547,89 @@ def run_pt_large_bench(args, sk, sh):
     return {"metric": "PT estimates beyond n = 24 (Tables 7 / 8)", "unit": "relative error",
             "config": {"workload": "32 temperatures x 4096 ladders, Skolem n=25..33, "
                                    "Langford n=27..32"},
+            "results": out}
+
+
+EXACT_S12, EXACT_L12 = 227968, 108144                  # Tables 7 / 8
+
+
+def run_pt_gain_bench(args, sk, sh):
+    """What the trained proposal network gains per iteration and what it
+    costs in GPU time: plain and learned chains at equal iterations on
+    S(12), L(12) and S(16), the pilot-tuned 32-rung ladder, 512 ladders, 10 %
+    burn-in, six seeds per point (mean relative error and its standard
+    error over the seeds, mean move acceptance at the middle rung, GPU time
+    of the chains).  The network is trained on 262144 final states of plain
+    runs on the same ladder (5 epochs, minibatch 4096, Adam 1e-3,
+    beta* = 2)."""
+    import numpy as np
+    cases = [(0, 12, EXACT_S12), (1, 12, EXACT_L12), (0, 16, EXACT_S[16])]
+    budgets = (400, 800, 1600, 3200)
+    L, seeds = 512, 6
+    out = {}
+    for v, n, exact in cases[:args.pt_cases]:
+        beta = sk.tune_ladder(v, n, 32, 32.0, 0)
+        states = np.concatenate([
+            sk.pt_run(v, n, beta, 1024, 1000, 0, 100 + s, want_final=True)["final_slots"].reshape(-1, n)
+            for s in range(8)])
+        model = sk.Mlp(v, n, L * 32, seed=1)
+        loss, train_ms = model.train(states, epochs=5, batch=4096, lr=1e-3, beta_star=2.0, seed=1)
+        rows = []
+        for iters in budgets:
+            row = {"iterations": iters}
+            for name, mdl in (("plain", None), ("learned", model)):
+                errs, acc, ms = [], [], 0.0
+                for s in range(seeds):
+                    est, rep = sk.pt_estimate(v, n, iters, ladders=L, seed=1000 + s, beta=beta,
+                                              model=mdl, stream=sh)
+                    errs.append(est / exact - 1)
+                    acc.append(rep["acc_move"][16])
+                    ms += rep["kernel_ms"]
+                row[name] = {"rel_error": float(np.mean(errs)),
+                             "se": float(np.std(errs, ddof=1) / np.sqrt(seeds)),
+                             "acc_move_mid": float(np.mean(acc)), "gpu_ms_per_run": ms / seeds}
+            rows.append(row)
+        model.close()
+        out[f"{'SL'[v]}({n})"] = {"train_loss": loss, "train_ms": train_ms, "rows": rows}
+    return {"metric": "PT error at equal iterations and GPU time, learned vs plain proposal",
+            "unit": "relative error",
+            "config": {"workload": "32 temperatures x 512 ladders, S(12), L(12), S(16), 6 seeds",
+                       "training": "262144 plain-PT states, 5 epochs, Adam 1e-3"},
+            "results": out}
+
+
+def run_pt_bias_bench(args, sk, sh):
+    """Is there a bias of the tempering estimate at the largest orders?  The
+    orders of Tables 7 / 8 from 27 up, each estimated with the pilot-tuned
+    32-rung ladder topped at beta_max = 32, 48 and 64, and with beta_max = 32
+    and four times the iterations; per run the estimate and its standard
+    error (16 groups of 256 ladders), the smallest exchange acceptance of
+    the ladder and P(E = 0) at the top rung (the last ratio of Algorithm 2).
+    32 rungs is the most a ladder has (one warp, one rung per lane)."""
+    cases = [(0, 28), (0, 29), (1, 27), (1, 28), (0, 32), (0, 33), (1, 31), (1, 32)]
+    base = args.pt_budgets[0]
+    variants = [(32.0, base), (48.0, base), (64.0, base), (32.0, 4 * base)]
+    out = {}
+    for v, n in cases[:args.pt_cases]:
+        exact = (EXACT_S if v == 0 else EXACT_L).get(n)
+        paper = (PAPER_PT_S if v == 0 else PAPER_PT_L)[n]
+        rows = []
+        for bmax, budget in variants:
+            est, rep = sk.pt_estimate(v, n, budget, ladders=4096, seed=7, beta_max=bmax, stream=sh)
+            M = rep["rungs"]
+            rows.append({"beta_max": bmax, "iterations": budget, "estimate": est,
+                         "rel_stderr": rep["rel_stderr"],
+                         "rel_error": (est / exact - 1) if exact else None,
+                         "z_vs_exact": ((est / exact - 1) / rep["rel_stderr"]) if exact else None,
+                         "vs_paper_estimate": est / paper - 1,
+                         "min_exchange_acceptance": min(rep["acc_swap"][:M - 1]),
+                         "p_top_E0": rep["ratio"][M - 1], "beta": rep["beta"],
+                         "gpu_ms": rep["kernel_ms"]})
+        out[f"{'SL'[v]}({n})"] = rows
+    return {"metric": "PT estimates at n = 27..33 across ladders (beta_max) and run lengths",
+            "unit": "relative error",
+            "config": {"workload": "32 temperatures x 4096 ladders, Skolem n=28,29,32,33, "
+                                   "Langford n=27,28,31,32"},
             "results": out}
 
 
