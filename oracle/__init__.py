@@ -56,6 +56,10 @@ def _load():
             lib.orc_summand.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, u64p]
             lib.orc_partial_sum_mod.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_uint64, ctypes.c_uint64, u64p]
+            lib.orc_backtrack_hole.argtypes = [ctypes.c_int, ctypes.c_int, u64p]
+            lib.orc_signed_sum_hole.argtypes = [ctypes.c_int, ctypes.c_int, u64p]
+            lib.orc_partial_sum_mod_hole.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                     ctypes.c_uint64, ctypes.c_uint64, u64p]
             lib.orc_ie_count.argtypes = [ctypes.c_int, ctypes.c_int, u64p]
             lib.orc_ie_partial_sum_mod.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                    ctypes.c_uint64, ctypes.c_uint64, u64p]
@@ -145,6 +149,37 @@ def partial_sum_mod(variant: int, n: int, m: int, q: int, p: int) -> int:
     lib = _load()
     out = ctypes.c_uint64()
     _check(lib.orc_partial_sum_mod(variant, n, m, q, p, ctypes.byref(out)), "partial_sum_mod")
+    return out.value
+
+
+def backtrack_count_hole(n: int, hole: int) -> int:
+    """O1 for extended Skolem sequences (Sec. 1.2): positions 1..2n+1 except
+    `hole`, differences 1..n; reflections distinct."""
+    lib = _load()
+    c = ctypes.c_uint64()
+    _check(lib.orc_backtrack_hole(n, hole, ctypes.byref(c)), "backtrack_hole")
+    return c.value
+
+
+def coefficient_hole(n: int, hole: int) -> int:
+    """Lemma 2.1 with Lemma 2.2 on the same position set: Algorithm 1's
+    half-sum divided by 2^{2n-1}."""
+    lib = _load()
+    out = (ctypes.c_uint64 * 2)()
+    _check(lib.orc_signed_sum_hole(n, hole, out), "signed_sum_hole")
+    s = _s128(out[0], out[1])
+    div = 1 << (2 * n - 1)
+    if s % div:
+        raise ArithmeticError(f"signed sum {s} not divisible by 2^{2 * n - 1}")
+    return s // div
+
+
+def partial_sum_mod_hole(n: int, hole: int, m: int, q: int, p: int) -> int:
+    """One block of that half-sum modulo p (free variables: the positions
+    below max P in increasing order; the low m run, the rest fixed by q)."""
+    lib = _load()
+    out = ctypes.c_uint64()
+    _check(lib.orc_partial_sum_mod_hole(n, hole, m, q, p, ctypes.byref(out)), "partial_sum_mod_hole")
     return out.value
 
 

@@ -23,6 +23,10 @@
  *                            (the low m free variables run, the rest fixed),
  *                            reduced modulo a given prime (Sec. 2.2: residues
  *                            modulo co-primes).
+ *   orc_backtrack_hole, orc_signed_sum_hole, orc_partial_sum_mod_hole --
+ *                            the same three for extended Skolem sequences
+ *                            (Sec. 1.2: the hook anywhere): positions 1..2n+1
+ *                            except one hole, differences 1..n.
  *   orc_ie_count          -- the inclusion-exclusion count (Sec. 2, the
  *                            third approach, after Larsen): over every set S
  *                            of avoided positions, (-1)^{|S|} times the
@@ -65,7 +69,7 @@
 typedef unsigned __int128 u128;
 typedef __int128 s128;
 
-#define ORC_MAXN 40
+#define ORC_MAXN 64      /* the paper's largest order: its closing S(64) estimate */
 #define ORC_MAXSPAN (2 * ORC_MAXN + 2)
 
 /* ------------------------------------------------------------------ layout */
@@ -268,6 +272,7 @@ int orc_partial_sum_mod(int variant, int n, int m, uint64_t q, uint64_t p, uint6
     if (orc_layout(variant, n, &span, present, d)) return -1;
     int nfree = 2 * n - 1;
     if (m < 0 || m > nfree || m > 40 || p < 3 || p > ((uint64_t)1 << 62)) return -1;
+    if (nfree - m > 64) return -1;             /* q holds the fixed variables */
     int top = 0;
     for (int i = 1; i <= span; i++) if (present[i]) top = i;
     int x[ORC_MAXSPAN + 2];
@@ -277,6 +282,92 @@ int orc_partial_sum_mod(int variant, int n, int m, uint64_t q, uint64_t p, uint6
         for (int i = 0; i < nfree; i++) {
             int bit = (i < m) ? (int)((w >> i) & 1) : (int)((q >> (i - m)) & 1);
             x[i + 1] = bit ? -1 : 1;
+        }
+        x[top] = 1;
+        int sign = 1;
+        for (int i = 1; i <= span; i++) if (present[i]) sign *= x[i];
+        uint64_t prod = 1;
+        for (int k = 1; k <= n; k++) {
+            long s = 0;
+            for (int a = 1; a + d[k] <= span; a++) s += (long)x[a] * x[a + d[k]];
+            prod = mulmod(prod, to_res(s, p), p);
+        }
+        if (sign < 0) prod = prod ? p - prod : 0;
+        acc = (acc + prod) % p;
+    }
+    *out = acc;
+    return 0;
+}
+
+/* ------------------------------- extended Skolem sequences (one hole) */
+
+/* Sec. 1.2: extended Skolem sequences (Abrham and Kotzig) distribute the
+ * numbers over 1..2n+1 with one position -- the hole -- left empty, pairs of
+ * k at distance k.  hole = 2n is the hooked problem, hole = n+1 Rosa's (the
+ * skip in the middle), hole = 2n+1 or 1 the Skolem problem on 2n positions. */
+static int layout_hole(int n, int hole, int *span, int *present, int *d)
+{
+    if (n < 1 || n > ORC_MAXN || hole < 1 || hole > 2 * n + 1) return -1;
+    *span = 2 * n + 1;
+    for (int i = 0; i <= *span; i++) present[i] = (i >= 1 && i != hole);
+    for (int k = 1; k <= n; k++) d[k] = k;
+    return 0;
+}
+
+int orc_backtrack_hole(int n, int hole, uint64_t *count)
+{
+    bt_state *st = (bt_state *)calloc(1, sizeof(bt_state));
+    if (!st) return -1;
+    if (layout_hole(n, hole, &st->span, st->present, st->d)) { free(st); return -1; }
+    st->n = n;
+    bt_place(st, n);
+    *count = st->count;
+    free(st);
+    return 0;
+}
+
+/* Algorithm 1 over the ±1 assignments of the 2n positions of that P, with
+ * the variable at max P held at +1 (Lemma 2.2): the half-sum S as a
+ * two's-complement 128-bit integer, out[0..1]. */
+int orc_signed_sum_hole(int n, int hole, uint64_t *out)
+{
+    ss_job j;
+    memset(&j, 0, sizeof(j));
+    if (layout_hole(n, hole, &j.span, j.present, j.d)) return -1;
+    j.n = n;
+    int top = 0;
+    for (int p = 1; p <= j.span; p++) if (j.present[p]) top = p;
+    for (int p = 1; p <= j.span; p++)
+        if (j.present[p] && p != top) j.var_pos[j.nvar++] = p;
+    j.fixed_top = top;
+    if (j.nvar > 40) return -1;
+    j.lo = 0;
+    j.hi = (uint64_t)1 << j.nvar;
+    ss_worker(&j);
+    out[0] = (uint64_t)j.sum;
+    out[1] = (uint64_t)(j.sum >> 64);
+    return 0;
+}
+
+/* One block of that half-sum modulo p: the free variables are the positions
+ * of P below max P in increasing order (variable i = the i-th of them); the
+ * low m run over both values, variable m+b is -1 iff bit b of q is set. */
+int orc_partial_sum_mod_hole(int n, int hole, int m, uint64_t q, uint64_t p, uint64_t *out)
+{
+    int span, present[ORC_MAXSPAN + 1], d[ORC_MAXN + 1], pos[ORC_MAXSPAN];
+    if (layout_hole(n, hole, &span, present, d)) return -1;
+    int top = 0, nfree = 0;
+    for (int i = 1; i <= span; i++) if (present[i]) top = i;
+    for (int i = 1; i <= span; i++) if (present[i] && i != top) pos[nfree++] = i;
+    if (m < 0 || m > nfree || m > 40 || nfree - m > 63 || p < 3 || p > ((uint64_t)1 << 62))
+        return -1;
+    int x[ORC_MAXSPAN + 2];
+    uint64_t acc = 0;
+    for (uint64_t w = 0; w < ((uint64_t)1 << m); w++) {
+        memset(x, 0, sizeof(x));
+        for (int i = 0; i < nfree; i++) {
+            int bit = (i < m) ? (int)((w >> i) & 1) : (int)((q >> (i - m)) & 1);
+            x[pos[i]] = bit ? -1 : 1;
         }
         x[top] = 1;
         int sign = 1;
