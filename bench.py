@@ -264,6 +264,8 @@ def run_extra(args, world, rank, local):
         line = run_pt_bias_bench(args, sk, sh)
     elif args.config == "pt-gain":
         line = run_pt_gain_bench(args, sk, sh)
+    elif args.config == "train":
+        line = run_train_bench(args, sk, sh)
     else:
         import tempfile
         res = {}
@@ -404,8 +406,10 @@ SLICE_CASES = [(0, 21), (1, 23), (0, 24), (1, 24), (0, 25), (1, 27), (0, 28), (1
 def run_slices_bench(args, sk, sh):
     """Timed slices of the large exact counts: the first 2^slice_bits terms
     (one checkpoint chunk) of S(21) .. S(29), L(23) .. L(31) and hooked
-    Skolem n = 30, four moduli, Lemma 2.4 on where it applies, with the
-    plan the library picks for the whole count.  A full count's time is
+    Skolem n = 30, four moduli, Lemma 2.4 on where it applies.  The walk
+    width is the plan's, capped so that a slice holds at least 2^17 work items
+    (the GPU holds ~78k threads; at n = 31 the plan walks 2^31 terms per item,
+    which a slice could not spread over the GPU).  A full count's time is
     projected from the slice's rate (every work item walks the same Gray
     schedule, so the rate does not depend on which items are timed)."""
     import tempfile
@@ -418,14 +422,15 @@ def run_slices_bench(args, sk, sh):
         if os.path.exists(path):
             os.remove(path)
         plan = sk.count_plan(v, n, nprimes=4, checkpoint=path, symmetry=sym)
-        m = plan["walk_bits"]
+        m = min(plan["walk_bits"], max(plan["inner_bits"], args.slice_bits - 17))
+        plan = sk.count_plan(v, n, nprimes=4, checkpoint=path, symmetry=sym, walk_bits=m)
         chunk = 1 << max(0, args.slice_bits - m)
         best = None
         for rep_i in range(2):                  # first call warms the kernel up
             if os.path.exists(path):
                 os.remove(path)
             c, rep = sk.count_ex(v, n, nprimes=4, checkpoint=path, chunk_items=chunk,
-                                 max_chunks=1, symmetry=sym, stream=sh)
+                                 max_chunks=1, symmetry=sym, stream=sh, walk_bits=m)
             # one chunk; a slice as large as the count is the whole count
             assert rep["chunks_done"] == 1 and (c is None) == (rep["chunks_total"] > 1), rep
             best = rep["kernel_ms"] if best is None else min(best, rep["kernel_ms"])
@@ -464,7 +469,8 @@ EXACT_S = {16: 700078384, 20: 5717789399488, 24: 102388058845620672,
 EXACT_L = {16: 326721800, 20: 2636337861200, 24: 46845158056515936,
            27: 111683611098764903232, 28: 1607383260609382393152}  # Table 8, exact column
 # the paper's own tempering estimates (Tables 7 / 8, approximate column)
-PAPER_PT_S = {25: 1.317e18, 28: 3.523e21, 29: 5.294e22, 32: 2.213e26, 33: 3.614e27}
+PAPER_PT_S = {25: 1.317e18, 28: 3.523e21, 29: 5.294e22, 32: 2.213e26, 33: 3.614e27,
+              64: 4.1e70}                                  # S(64): the closing section
 PAPER_PT_L = {27: 1.115e20, 28: 1.603e21, 31: 5.381e24, 32: 8.812e25}
 
 
@@ -529,7 +535,8 @@ def run_pt_large_bench(args, sk, sh):
     """Plain tempering beyond the exact workloads: the orders of Tables 7 / 8
     above 24, errors against the exact counts where the paper has them and
     the estimate beside the paper's own tempering estimate."""
-    cases = [(0, 25), (0, 28), (0, 29), (1, 27), (1, 28), (0, 32), (0, 33), (1, 31), (1, 32)]
+    cases = [(0, 25), (0, 28), (0, 29), (1, 27), (1, 28), (0, 32), (0, 33), (1, 31), (1, 32),
+             (0, 64)]
     out = {}
     for v, n in cases[:args.pt_cases]:
         exact = (EXACT_S if v == 0 else EXACT_L).get(n)
@@ -551,6 +558,39 @@ def run_pt_large_bench(args, sk, sh):
 
 
 EXACT_S12, EXACT_L12 = 227968, 108144                  # Tables 7 / 8
+
+
+def run_train_bench(args, sk, sh):
+    """Training of the proposal network: one epoch of Adam over 2^20 plain-
+    tempering states (minibatch 4096, 256 steps) for S(20), with the forward
+    and backward GEMMs on tcgen05 and on mma.sync; device time per step
+    (sk_mlp_train's CUDA events), best of `steps` epochs after one warm-up
+    epoch.  Both start from the same weights."""
+    import numpy as np
+    v, n = 0, 20
+    beta = sk.tune_ladder(v, n, 32, 32.0, 0)
+    states = np.concatenate([
+        sk.pt_run(v, n, beta, 4096, 500, 0, 300 + s, want_final=True)["final_slots"].reshape(-1, n)
+        for s in range(8)])[:1 << 20]
+    out = {}
+    for name, tc in (("tcgen05", True), ("mma_sync", False)):
+        model = sk.Mlp(v, n, 4096, seed=1)
+        model.set_gemm(tc)
+        model.train(states, epochs=1, batch=4096, lr=1e-3, beta_star=2.0, seed=1)
+        best = None
+        for _ in range(max(1, args.steps)):
+            loss, ms = model.train(states, epochs=1, batch=4096, lr=1e-3, beta_star=2.0, seed=2)
+            best = ms if best is None else min(best, ms)
+        model.check()
+        model.close()
+        steps = states.shape[0] // 4096
+        out[name] = {"ms_per_epoch": best, "ms_per_step": best / steps, "steps": steps,
+                     "final_loss": loss}
+    return {"metric": "proposal-network training step time, tcgen05 vs mma.sync GEMMs",
+            "unit": "ms", "config": {"workload": "S(20) network (40 -> 256 -> 256 -> 590 moves), "
+                                                 "minibatch 4096, 2^20 plain-PT states"},
+            "results": out,
+            "speedup_tcgen05": out["mma_sync"]["ms_per_step"] / out["tcgen05"]["ms_per_step"]}
 
 
 def run_pt_gain_bench(args, sk, sh):
@@ -756,11 +796,17 @@ def main():
     ap.add_argument("--pt-budgets", type=int, nargs="+", default=[2000, 8000, 32000])
     ap.add_argument("--pt-learned-budgets", type=int, nargs="+", default=[200, 800])
     ap.add_argument("--pt-samples", type=int, default=10_000_000)
-    ap.add_argument("--pt-cases", type=int, default=9, help="first cases of --config pt / pt-large")
-    ap.add_argument("--config", default="mid", choices=["mid", "batch", "large", "pt", "pt-large"],
+    ap.add_argument("--pt-cases", type=int, default=10, help="first cases of --config pt / pt-large")
+    ap.add_argument("--slice-bits", type=int, default=40, help="terms per slice of --config slices (log2)")
+    ap.add_argument("--config", default="mid",
+                    choices=["mid", "batch", "large", "slices", "ie", "symmetry", "pt", "pt-large",
+                             "pt-bias", "pt-gain", "train"],
                     help="mid: the headline workload; the others: extra measurements")
     ap.add_argument("--nmax", type=int, default=22, help="largest n of --config batch")
+    ap.add_argument("--no-autotune", action="store_true", help="--config batch without the tuned run")
     ap.add_argument("--ckpt-dir", default=None, help="checkpoint directory of --config large")
+    ap.add_argument("--symmetries", type=int, nargs="+", default=[0, 1],
+                    help="--config large: SK_SYMMETRY_* options to run (0: Lemma 2.2, 1: + 2.4, 2: + 2.3)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -281,7 +281,11 @@ typedef struct sk_pt_report {
  * iterations per ladder (each one move per rung plus one exchange phase),
  * 1 <= budget < 2^32.  out (host): 1/2 Z(0) prod_j Ratio(j), reflections
  * identified, with Z(0) = prod_k (2n - d_k).  Skolem and Langford,
- * 2 <= n <= 40.  Deterministic for a given seed. */
+ * 2 <= n <= 64 (the learned proposal: n <= 40).  Deterministic for a given
+ * seed.  Above n = 40 a ladder's tables (16-bit energy histogram of 2n+1
+ * rows, start slots, bin counts) need more shared memory than 28 warps per
+ * SM can hold, so fewer ladders are resident at once and a run of 4096
+ * ladders takes more than one wave. */
 int pt_estimate(int variant, int n, uint64_t budget, double *out);
 int pt_estimate_ex(int variant, int n, uint64_t budget, const sk_pt_opts *opts, double *out,
                    sk_pt_report *rep);

@@ -380,7 +380,7 @@ static size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
 int mlp_create(int variant, int n, int max_batch, uint64_t seed, Mlp** out) {
   if (variant != SK_SKOLEM && variant != SK_LANGFORD) return SK_EINVAL;
-  if (n < 2 || n > kPtMaxN || max_batch < 128 || max_batch % 128) return SK_EINVAL;
+  if (n < 2 || n > kMlpMaxN || max_batch < 128 || max_batch % 128) return SK_EINVAL;
   int st = check_device();
   if (st) return st;
   Mlp* m = new Mlp;

@@ -27,7 +27,8 @@
 namespace sk {
 
 constexpr int kPtMaxRungs = 32;
-constexpr int kPtMaxN = 40;
+constexpr int kPtMaxN = 64;      // plain chains (the paper's closing estimate is S(64))
+constexpr int kMlpMaxN = 40;     // the learned proposal (its move table, input width 128)
 constexpr int kPtErrorGroups = 16;   // ladder groups behind pt_estimate's standard error
 
 struct PtParams {

@@ -43,7 +43,7 @@ struct LearnedDev {
 // every move m (moves of pair k are off[k] .. off[k+1]-1), so a lane tests
 // "m is a valid move" (its slot is not the pair's current one) with two
 // shared-memory loads.
-constexpr int kMaxMoves = 2560;        // sum_k (2n - d_k) for n <= kPtMaxN
+constexpr int kMaxMoves = 2560;        // sum_k (2n - d_k) for n <= kMlpMaxN
 struct MoveMaps {
   unsigned char k[kMaxMoves];
   unsigned char s[kMaxMoves];

@@ -34,7 +34,7 @@ def test_count_options(variant, n, kw):
 @pytest.mark.parametrize("args", [
     (2, 8, [0.0, 1.0], 4, 10, 0, 1),                # hooked: no tempering variant
     (0, 1, [0.0, 1.0], 4, 10, 0, 1),                # n < 2
-    (0, 41, [0.0, 1.0], 4, 10, 0, 1),               # above the largest order
+    (0, 65, [0.0, 1.0], 4, 10, 0, 1),               # above the largest order
     (0, 8, [float(j) for j in range(33)], 4, 10, 0, 1),   # 33 rungs
     (0, 8, [0.0, 1.0], 0, 10, 0, 1),                # no ladder
     (0, 8, [1.0, 0.5], 4, 10, 0, 1),                # decreasing ladder
@@ -55,7 +55,7 @@ def test_pt_run_arguments(args):
     (0, 8, 1000, {"rungs": 33}),
     (0, 8, 1000, {"burnin_frac": 1.0}),             # burn-in would take every iteration
     (2, 8, 1000, {}),
-    (0, 41, 1000, {}),
+    (0, 65, 1000, {}),
 ])
 def test_pt_estimate_arguments(variant, n, budget, kw):
     with pytest.raises(sk.SkolemError) as e:
@@ -89,3 +89,10 @@ def test_reversal_refusals_before_device_work():
             sk.count_plan(*args, symmetry=sk.SYMMETRY_REVERSAL, **kw)
         assert e.value.status == sk.SK_EINVAL, (args, kw)
 
+
+def test_learned_proposal_orders():
+    # the network's move table and input width hold n <= 40; the plain
+    # chains go to n = 64
+    with pytest.raises(sk.SkolemError) as e:
+        sk.Mlp(0, 41, 128)
+    assert e.value.status == sk.SK_EINVAL

@@ -60,7 +60,7 @@ def test_argument_checks():
     beta = np.linspace(0.0, 4.0, 4)
     h = np.ones((4, 9), dtype=np.uint64)
     for args in ((2, 4, beta, h), (0, 1, beta, np.ones((4, 3), np.uint64)),
-                 (0, 4, beta[::-1].copy(), h), (0, 41, beta, np.ones((4, 83), np.uint64))):
+                 (0, 4, beta[::-1].copy(), h), (0, 65, beta, np.ones((4, 131), np.uint64))):
         with pytest.raises(sk.SkolemError) as e:
             sk.pt_estimate_hist(*args)
         assert e.value.status == sk.SK_EINVAL
