@@ -270,7 +270,7 @@ def run_extra(args, world, rank, local):
         import tempfile
         res = {}
         names = {sk.SYMMETRY_NEGATION: "", sk.SYMMETRY_NEGATION_EVEN: " lemma 2.4",
-                 sk.SYMMETRY_REVERSAL: " lemma 2.3"}
+                 sk.SYMMETRY_REVERSAL: " lemma 2.3", sk.SYMMETRY_REVERSAL_EVEN: " lemmas 2.3 + 2.4"}
         want = {(0, 24): EXACT_S[24], (1, 24): EXACT_L[24]}
         for sym in args.symmetries:
             for v, n in ((0, 24), (1, 24)):
@@ -336,13 +336,14 @@ def run_batch_bench(args, sk, sh):
 def run_symmetry_bench(args, sk, sh):
     """What the extra symmetries buy on the mid-size workload: every job with
     Lemma 2.2 alone (2^{2n-1} terms), with Lemma 2.4 on top (half of them,
-    in the existence classes; none outside) and with Lemma 2.3 on top (the
-    mirrored walk, about half), best of `steps` runs each.  The counts must
+    in the existence classes; none outside), with Lemma 2.3 on top (the
+    mirrored walk, about half) and with both (about a quarter in the
+    existence classes), best of `steps` runs each.  The counts must
     agree.  Reported per job: kernel time, terms evaluated, and the
     equivalent rate 2^{2n-1} / time (the plain half-sum's terms per second of
     the run that skips some of them)."""
     modes = (("lemma_2_2", sk.SYMMETRY_NEGATION), ("lemma_2_4", sk.SYMMETRY_NEGATION_EVEN),
-             ("lemma_2_3", sk.SYMMETRY_REVERSAL))
+             ("lemma_2_3", sk.SYMMETRY_REVERSAL), ("lemma_2_3_and_2_4", sk.SYMMETRY_REVERSAL_EVEN))
     out, tot = {}, {name: 0.0 for name, _ in modes}
     for v, n in JOBS:
         row, c0 = {}, None
@@ -355,7 +356,9 @@ def run_symmetry_bench(args, sk, sh):
                 best = rep["kernel_ms"] if best is None else min(best, rep["kernel_ms"])
             row[name] = {"kernel_ms": best, "terms_evaluated": rep["terms"],
                          "walk_bits": rep["walk_bits"], "symmetry_used": rep["symmetry"],
-                         "equivalent_terms_per_s": (1 << (2 * n - 1)) / max(best, 1e-9) * 1e3}
+                         # no terms: the sum vanishes by Lemma 2.4's sign, nothing ran
+                         "equivalent_terms_per_s": ((1 << (2 * n - 1)) / best * 1e3
+                                                    if rep["terms"] else None)}
             tot[name] += best
         out[f"{'SL'[v]}({n})"] = row
     return {"metric": "exact count time with Lemma 2.2 alone, + Lemma 2.4, + Lemma 2.3",
@@ -537,14 +540,17 @@ def run_pt_large_bench(args, sk, sh):
     the estimate beside the paper's own tempering estimate."""
     cases = [(0, 25), (0, 28), (0, 29), (1, 27), (1, 28), (0, 32), (0, 33), (1, 31), (1, 32),
              (0, 64)]
+    if args.pt_only:
+        cases = [c for c in cases if f"{c[0]},{c[1]}" in args.pt_only]
     out = {}
     for v, n in cases[:args.pt_cases]:
         exact = (EXACT_S if v == 0 else EXACT_L).get(n)
         paper = (PAPER_PT_S if v == 0 else PAPER_PT_L)[n]
         rows = []
         for budget in args.pt_budgets:
-            est, rep = sk.pt_estimate(v, n, budget, ladders=4096, seed=budget, stream=sh)
-            rows.append({"iterations": budget, "estimate": est,
+            est, rep = sk.pt_estimate(v, n, budget, rungs=args.pt_rungs, ladders=4096, seed=budget,
+                                      stream=sh)
+            rows.append({"iterations": budget, "rungs": rep["rungs"], "estimate": est,
                          "rel_error": (est / exact - 1) if exact else None,
                          "paper_estimate": paper,
                          "paper_rel_error": (paper / exact - 1) if exact else None,
@@ -552,8 +558,8 @@ def run_pt_large_bench(args, sk, sh):
                          "gpu_ms": rep["kernel_ms"]})
         out[f"{'SL'[v]}({n})"] = rows
     return {"metric": "PT estimates beyond n = 24 (Tables 7 / 8)", "unit": "relative error",
-            "config": {"workload": "32 temperatures x 4096 ladders, Skolem n=25..33, "
-                                   "Langford n=27..32"},
+            "config": {"workload": f"{args.pt_rungs} temperatures x 4096 ladders, Skolem "
+                                   "n=25..33 and 64, Langford n=27..32"},
             "results": out}
 
 
@@ -645,19 +651,28 @@ def run_pt_bias_bench(args, sk, sh):
     and four times the iterations; per run the estimate and its standard
     error (16 groups of 256 ladders), the smallest exchange acceptance of
     the ladder and P(E = 0) at the top rung (the last ratio of Algorithm 2).
-    32 rungs is the most a ladder has (one warp, one rung per lane)."""
-    cases = [(0, 28), (0, 29), (1, 27), (1, 28), (0, 32), (0, 33), (1, 31), (1, 32)]
+    Then 64 rungs topped at beta_max = 32 (two warps a ladder): the same
+    top temperature with twice the rungs, closer neighbours and higher
+    exchange acceptance.  With --pt-rungs 64 only the 64-rung ladder runs,
+    for the base and four times the iterations."""
+    cases = [(0, 28), (0, 29), (1, 27), (1, 28), (0, 32), (0, 33), (1, 31), (1, 32), (0, 64)]
+    if args.pt_only:
+        cases = [c for c in cases if f"{c[0]},{c[1]}" in args.pt_only]
     base = args.pt_budgets[0]
-    variants = [(32.0, base), (48.0, base), (64.0, base), (32.0, 4 * base)]
+    variants = [(32.0, base, 32), (48.0, base, 32), (64.0, base, 32), (32.0, 4 * base, 32),
+                (32.0, base, 64)]
+    if args.pt_rungs == 64:
+        variants = [(32.0, base, 64), (32.0, 4 * base, 64)]
     out = {}
     for v, n in cases[:args.pt_cases]:
         exact = (EXACT_S if v == 0 else EXACT_L).get(n)
         paper = (PAPER_PT_S if v == 0 else PAPER_PT_L)[n]
         rows = []
-        for bmax, budget in variants:
-            est, rep = sk.pt_estimate(v, n, budget, ladders=4096, seed=7, beta_max=bmax, stream=sh)
+        for bmax, budget, rungs in variants:
+            est, rep = sk.pt_estimate(v, n, budget, rungs=rungs, ladders=4096, seed=7,
+                                      beta_max=bmax, stream=sh)
             M = rep["rungs"]
-            rows.append({"beta_max": bmax, "iterations": budget, "estimate": est,
+            rows.append({"beta_max": bmax, "iterations": budget, "rungs": M, "estimate": est,
                          "rel_stderr": rep["rel_stderr"],
                          "rel_error": (est / exact - 1) if exact else None,
                          "z_vs_exact": ((est / exact - 1) / rep["rel_stderr"]) if exact else None,
@@ -668,8 +683,8 @@ def run_pt_bias_bench(args, sk, sh):
         out[f"{'SL'[v]}({n})"] = rows
     return {"metric": "PT estimates at n = 27..33 across ladders (beta_max) and run lengths",
             "unit": "relative error",
-            "config": {"workload": "32 temperatures x 4096 ladders, Skolem n=28,29,32,33, "
-                                   "Langford n=27,28,31,32"},
+            "config": {"workload": "32 and 64 temperatures x 4096 ladders, Skolem "
+                                   "n=28,29,32,33,64, Langford n=27,28,31,32"},
             "results": out}
 
 
@@ -797,6 +812,10 @@ def main():
     ap.add_argument("--pt-learned-budgets", type=int, nargs="+", default=[200, 800])
     ap.add_argument("--pt-samples", type=int, default=10_000_000)
     ap.add_argument("--pt-cases", type=int, default=10, help="first cases of --config pt / pt-large")
+    ap.add_argument("--pt-rungs", type=int, default=32,
+                    help="temperatures a ladder, --config pt-large (pt-bias: 64 -> 64-rung rows only)")
+    ap.add_argument("--pt-only", nargs="+", default=None,
+                    help="--config pt-large / pt-bias: only these cases, as variant,n (e.g. 0,64)")
     ap.add_argument("--slice-bits", type=int, default=40, help="terms per slice of --config slices (log2)")
     ap.add_argument("--config", default="mid",
                     choices=["mid", "batch", "large", "slices", "ie", "symmetry", "pt", "pt-large",
@@ -806,7 +825,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="--config batch without the tuned run")
     ap.add_argument("--ckpt-dir", default=None, help="checkpoint directory of --config large")
     ap.add_argument("--symmetries", type=int, nargs="+", default=[0, 1],
-                    help="--config large: SK_SYMMETRY_* options to run (0: Lemma 2.2, 1: + 2.4, 2: + 2.3)")
+                    help="--config large: SK_SYMMETRY_* options to run (0: Lemma 2.2, 1: + 2.4, "
+                         "2: + 2.3, 3: + 2.3 + 2.4)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

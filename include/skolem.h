@@ -98,8 +98,22 @@ enum { SK_ARITH_LIMBS = 0, SK_ARITH_MONTGOMERY = 1 };
  * are evaluated; walk_bits (if given) must be even, at least twice the
  * unrolled inner width and at most 2n-2.  The result is the same.  Needs
  * n >= 6; smaller orders use SK_SYMMETRY_NEGATION (the report says which
- * was used).  Exact-digit form only (arith = SK_ARITH_LIMBS). */
-enum { SK_SYMMETRY_NEGATION = 0, SK_SYMMETRY_NEGATION_EVEN = 1, SK_SYMMETRY_REVERSAL = 2 };
+ * was used).  Exact-digit form only (arith = SK_ARITH_LIMBS).
+ * SK_SYMMETRY_REVERSAL_EVEN (Skolem and Langford): Lemmas 2.2, 2.3 and 2.4
+ * together.  Outside the existence classes the sum is 0 (Lemma 2.4's sign).
+ * Inside them, negating the odd positions keeps the summand, flips x_1 and
+ * keeps x_{2n}; it maps the mirrored walk's positions onto themselves and so
+ * carries every work item with x_1 = +1 onto one with x_1 = -1 of equal sum:
+ * only the x_1 = +1 items are evaluated and the sum is doubled, about a
+ * quarter of the 2^{2n-1} terms.  Same walk-width rules as
+ * SK_SYMMETRY_REVERSAL; n < 6 falls back to SK_SYMMETRY_NEGATION_EVEN (n >=
+ * 4) or SK_SYMMETRY_NEGATION. */
+enum {
+  SK_SYMMETRY_NEGATION = 0,
+  SK_SYMMETRY_NEGATION_EVEN = 1,
+  SK_SYMMETRY_REVERSAL = 2,
+  SK_SYMMETRY_REVERSAL_EVEN = 3
+};
 #define SK_MAX_PRIMES 4
 
 typedef struct { uint64_t lo, hi; } sk_u128;   /* unsigned 128-bit integer */
@@ -243,10 +257,14 @@ int skolem_autotune(int variant, int n, const sk_batch_opts *opts, sk_tune_resul
  * paper). */
 enum { SK_PT_PLAIN = 0, SK_PT_LEARNED = 1 };
 
-#define SK_PT_MAX_RUNGS 32
+#define SK_PT_MAX_RUNGS 64
+#define SK_PT_MAX_RUNGS_LEARNED 32
 
 typedef struct sk_pt_opts {
-  int rungs;              /* M temperatures, 1..32; 0 -> 32 */
+  int rungs;              /* M temperatures, 1..64 (the learned proposal: 2..32);
+                             0 -> 32.  Up to 32 rungs a ladder is one warp, lane
+                             j serving rung j; 33..64 rungs span two warps, whose
+                             rungs 31 and 32 exchange through shared memory */
   int ladders;            /* independent ladders run side by side; 0 -> 4096 */
   uint64_t seed;          /* Philox key */
   double burnin_frac;     /* leading fraction of iterations not counted;
@@ -291,7 +309,7 @@ int pt_estimate_ex(int variant, int n, uint64_t budget, const sk_pt_opts *opts, 
                    sk_pt_report *rep);
 
 /* The raw tempering run behind pt_estimate, for checks against a reference:
- * L ladders of M rungs with the given ladder beta (host, M values) for
+ * L ladders of M rungs (1..64) with the given ladder beta (host, M values) for
  * `iters` iterations, statistics after `burnin`.  Host outputs: hist
  * (M x (2n+1), counts of the energy E at each rung), acc_move / acc_swap
  * (M, may be NULL), final_slots (L x M x n start bins of pair k = 1..n at
@@ -362,10 +380,12 @@ int sk_mlp_train(void *model, const uint8_t *states, uint64_t count, int epochs,
  * moments). */
 int sk_mlp_get_train_state(const void *model, float *adam_m, float *adam_v, float *used,
                            int64_t *t);
-/* Selects the forward GEMM path of a model: 1 (default) the 5th-generation
- * tensor cores (tcgen05, accumulators in tensor memory), 0 warp-level
- * mma.sync.  sk_mlp_check returns SK_ETIMEOUT if a tensor-core wait of the
- * model ever gave up (the results of that call are then invalid). */
+/* Selects the GEMM path of a model's forward and backward: 1 (default) the
+ * 5th-generation tensor cores (tcgen05, accumulators in tensor memory; the
+ * backward's weight gradients summed over a K split in a fixed order, so a
+ * gradient is the same bits every call), 0 warp-level mma.sync.
+ * sk_mlp_check returns SK_ETIMEOUT if a tensor-core wait of the model ever
+ * gave up (the results of that call are then invalid). */
 int sk_mlp_set_gemm(void *model, int use_tensor_memory_path);
 int sk_mlp_check(void *model);
 /* The learned tempering run behind pt_estimate_ex with SK_PT_LEARNED, with
@@ -401,6 +421,32 @@ int skolem_item_residues(int variant, int n, int m, uint64_t q_lo, uint64_t coun
 int sk_count_from_residues(int variant, int n, int convention, int nprimes,
                            const uint64_t *primes, uint64_t parts, const uint64_t *residues,
                            sk_u128 *out);
+
+/* ------------------------------------------- extended Skolem sequences */
+
+/* The exact count of extended Skolem sequences (Sec. 1.2 names them, after
+ * Abrham and Kotzig): the numbers 1..n in pairs at distance k over the
+ * positions 1..2n+1 with one position -- `hole`, 1 <= hole <= 2n+1 -- left
+ * empty.  hole = 2n is the hooked problem, hole = n+1 Rosa's (the skip in
+ * the middle), holes 1 and 2n+1 the Skolem problem.  Lemma 2.1 on that
+ * position set, the half-sum of Lemma 2.2, residues and CRT as in
+ * skolem_count_ex (same options and report; symmetry must be
+ * SK_SYMMETRY_NEGATION).  Reversal maps the sequences of hole h onto those
+ * of hole 2n+2-h: a hole below n+1 is counted on its mirror image, and
+ * reflections are identified (SK_COUNT_REFLECTIONS_IDENTIFIED) only for
+ * holes 1, n+1 and 2n+1, whose position sets it maps onto themselves; any
+ * other hole returns the count as it is.  The hole is held out of the walk:
+ * a hole inside the unrolled inner block (n <= 4, holes near the middle)
+ * returns SK_EINVAL, as does a walk_bits above the (mirrored) hole's bit. */
+int sk_count_extended(int n, int hole, const sk_count_opts *opts, sk_u128 *out,
+                      sk_count_report *rep);
+
+/* Residues of single work items of that count for holes n+1..2n+1: the free
+ * variables are the positions of P below max P in increasing order; item q
+ * of walk width m fixes those beyond the first m (bit b of q -> variable
+ * m+b) and runs the first m.  Otherwise as skolem_item_residues. */
+int sk_extended_item_residues(int n, int hole, int m, uint64_t q_lo, uint64_t count, int nprimes,
+                              const uint64_t *primes, uint64_t *out);
 
 /* ------------------------------------------ inclusion-exclusion count */
 

@@ -19,6 +19,7 @@ REFLECTIONS_IDENTIFIED, COUNT_ALL = 0, 1
 ARITH_LIMBS, ARITH_MONTGOMERY = 0, 1
 SYMMETRY_NEGATION, SYMMETRY_NEGATION_EVEN = 0, 1      # Lemma 2.2; Lemmas 2.2 + 2.4
 SYMMETRY_REVERSAL = 2                                  # Lemmas 2.2 + 2.3
+SYMMETRY_REVERSAL_EVEN = 3                             # Lemmas 2.2 + 2.3 + 2.4
 MAX_N = 31
 MAX_IE_N = 24
 MAX_PRIMES = 4
@@ -127,7 +128,8 @@ class TuneResult(ctypes.Structure):
 BATCH_PERSISTENT, BATCH_PER_JOB = 0, 1
 PT_PLAIN, PT_LEARNED = 0, 1
 MLP_KEEP_ORDER = (1 << 64) - 1      # sk_mlp_train seed: minibatches in the given order
-PT_MAX_RUNGS = 32
+PT_MAX_RUNGS = 64
+PT_MAX_RUNGS_LEARNED = 32
 
 
 class PtOpts(ctypes.Structure):
@@ -191,6 +193,12 @@ def lib():
                                           ctypes.c_uint64, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_uint64),
                                           ctypes.POINTER(ctypes.c_uint64)]
+        L.sk_count_extended.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(CountOpts),
+                                        ctypes.POINTER(U128), ctypes.POINTER(CountReport)]
+        L.sk_extended_item_residues.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_uint64),
+                                                ctypes.POINTER(ctypes.c_uint64)]
         L.skolem_count_batch.argtypes = [ctypes.POINTER(Job), ctypes.c_int, ctypes.POINTER(BatchOpts),
                                          ctypes.POINTER(U128), ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(BatchReport)]
@@ -311,6 +319,30 @@ def count_inclusion_exclusion(variant, n: int, **kw):
         raise SkolemError(st, f"sk_count_inclusion_exclusion({variant}, {n})")
     r = rep.as_dict()
     return (out.value() if r["complete"] else None), r
+
+
+def count_extended(n: int, hole: int, **kw):
+    """sk_count_extended: (count or None if incomplete, report dict) of the
+    extended Skolem sequences with the given hole; keywords as count_ex."""
+    o = _opts(**kw)
+    out = U128()
+    rep = CountReport()
+    st = lib().sk_count_extended(n, hole, ctypes.byref(o), ctypes.byref(out), ctypes.byref(rep))
+    if st != SK_OK:
+        raise SkolemError(st, f"sk_count_extended({n}, {hole})")
+    r = rep.as_dict()
+    return (out.value() if r["complete"] else None), r
+
+
+def extended_item_residues(n: int, hole: int, m: int, q_lo: int, count_: int, primes):
+    """sk_extended_item_residues: list of per-item lists of residues."""
+    k = len(primes)
+    P = (ctypes.c_uint64 * k)(*primes)
+    out = (ctypes.c_uint64 * (count_ * k))()
+    st = lib().sk_extended_item_residues(n, hole, m, q_lo, count_, k, P, out)
+    if st != SK_OK:
+        raise SkolemError(st, "sk_extended_item_residues")
+    return [list(out[i * k:(i + 1) * k]) for i in range(count_)]
 
 
 def ie_item_residues(variant, n: int, m: int, q_lo: int, count_: int, primes):
@@ -499,8 +531,9 @@ def tune_ladder(variant, n: int, rungs: int = 32, beta_max: float = 32.0, seed: 
 
 
 def pt_estimate(variant, n: int, budget: int, rungs=0, ladders=0, seed=0, burnin_frac=0.0,
-                beta=None, beta_max=0.0, model=None, stream=None):
-    """pt_estimate_ex: (estimate, report dict)."""
+                beta=None, beta_max=0.0, model=None, stream=None, proposal=None):
+    """pt_estimate_ex: (estimate, report dict).  proposal defaults to PT_LEARNED
+    with a model, else PT_PLAIN."""
     np = _np()
     o = PtOpts()
     o.rungs, o.ladders, o.seed, o.burnin_frac, o.beta_max = rungs, ladders, seed, burnin_frac, beta_max
@@ -512,6 +545,8 @@ def pt_estimate(variant, n: int, budget: int, rungs=0, ladders=0, seed=0, burnin
     if model is not None:
         o.proposal = PT_LEARNED
         o.model = model.handle
+    if proposal is not None:
+        o.proposal = proposal
     o.stream = stream
     out = ctypes.c_double()
     rep = PtReport()

@@ -18,7 +18,8 @@ enum GemmEpi {
   EPI_F32 = 0,          // C (float) = acc + bias
   EPI_BF16_RELU = 1,    // C (bf16)  = relu(acc + bias)
   EPI_BF16_MASK = 2,    // C (bf16)  = acc where aux > 0, else 0
-  EPI_ATOMIC = 3        // C (float) += acc
+  EPI_ATOMIC = 3,       // C (float) += acc
+  EPI_BF16 = 4          // C (bf16)  = acc + bias
 };
 
 struct GemmArgs {
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(256) gemm_bf16_kernel(GemmArgs g) {
           atomicAdd(C + 1, v1);
           continue;
         }
-        if (g.bias && (EPI == EPI_F32 || EPI == EPI_BF16_RELU)) {
+        if (g.bias && (EPI == EPI_F32 || EPI == EPI_BF16_RELU || EPI == EPI_BF16)) {
           v0 += g.bias[col];
           v1 += g.bias[col + 1];
         }
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(256) gemm_bf16_kernel(GemmArgs g) {
           if (EPI == EPI_BF16_RELU) {
             v0 = fmaxf(v0, 0.f);
             v1 = fmaxf(v1, 0.f);
-          } else {
+          } else if (EPI == EPI_BF16_MASK) {
             const __nv_bfloat162 a2 =
                 *(const __nv_bfloat162*)(g.aux + (size_t)row * g.ldc + col);
             if (!(__bfloat162float(a2.x) > 0.f)) v0 = 0.f;

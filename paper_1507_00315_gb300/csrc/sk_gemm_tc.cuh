@@ -1,8 +1,15 @@
 // sk_gemm_tc.cuh -- BF16 GEMM on the 5th-generation tensor cores (tcgen05)
-// for the proposal network's forward pass: C[M x N] = A[M x K] * B^T + bias,
-// A row-major [M][K] (activations), B stored [N][K] (the weights kept
-// K-major), FP32 accumulation in tensor memory, fused bias (+ ReLU -> bf16)
-// epilogue.  M % 128 == 0, N % 256 == 0, K % 64 == 0, K <= 256.
+// for the proposal network: C[M x N] = A[M x K] * B^T (+ bias), A row-major
+// [M][K], B stored [N][K] (both K-major), FP32 accumulation in tensor
+// memory.  M % 128 == 0, N % 256 == 0, K % 64 == 0.  Epilogues: FP32 (+ bias)
+// -- the logits, and the partial products of a K split; BF16 ReLU(+ bias) --
+// the hidden layers; BF16 masked by an auxiliary matrix (C = acc where
+// aux > 0) -- the backward's activation gradients.  The B operand is either
+// resident (the forward: K <= 256, loaded once per CTA) or streamed slice by
+// slice beside A through the stage ring (the backward: any K).  A K split
+// (ksplit > 1) gives each CTA a range of K slices and writes its partial
+// product to rows ks * M .. ks * M + M - 1 of C (FP32), summed afterwards in
+// a fixed order.
 //
 // Persistent and warp-specialised, one CTA (6 warps) per SM:
 //   * every CTA owns one 256-wide column tile of B for the whole launch: its
@@ -38,6 +45,10 @@ constexpr int kTcStage = 32 * 128;                            // staging: 32 row
 constexpr int kTcThreads = 192;                               // 6 warps
 constexpr int kTcSmem =
     (kTcMaxK / kTcBK) * kTcSliceB + kTcStages * kTcSliceA + 4 * 2 * kTcStage + 1024;
+// streamed B: each stage of the ring holds an A slice and a B slice
+constexpr int kTcSmemStream = kTcStages * (kTcSliceA + kTcSliceB) + 4 * 2 * kTcStage + 1024;
+
+enum { kTcEpiF32 = 0, kTcEpiReluBf16 = 1, kTcEpiMaskBf16 = 2, kTcEpiBf16 = 3 };
 constexpr unsigned kTcWaitLimit = 1u << 24;                   // polls
 constexpr unsigned long long kTcWaitNs = 2000000000ULL;       // and at most 2 s
 
@@ -45,6 +56,9 @@ struct TcGemmArgs {
   int M, N, K;
   const float* bias;              // [N] or null
   unsigned* err;                  // set nonzero if a wait gave up
+  int ksplit;                     // K ranges (0 or 1: none); needs K / 64 % ksplit == 0
+  const __nv_bfloat16* aux;       // kTcEpiMaskBf16: [M][ldaux], C = acc where aux > 0
+  int ldaux;
 };
 
 __device__ __forceinline__ unsigned tc_smem_u32(const void* p) {
@@ -118,12 +132,18 @@ __host__ __device__ constexpr unsigned tc_idesc(int M, int N) {
          ((unsigned)(M >> 4) << 24);
 }
 
-// BF16 = 1: C = bf16(relu(acc + bias)); 0: C = fp32 (acc + bias).
-template <int BF16>
+// EPI: kTcEpiF32 C = fp32 (acc + bias); kTcEpiReluBf16 C = bf16(relu(acc +
+// bias)); kTcEpiMaskBf16 C = bf16(acc) where aux > 0, else 0; kTcEpiBf16 C =
+// bf16(acc + bias).  STREAMB: the B
+// slices travel with the A slices through the ring instead of staying
+// resident (any K).
+template <int EPI, bool STREAMB>
 __global__ void __launch_bounds__(kTcThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap amap,
                    const __grid_constant__ CUtensorMap bmap,
                    const __grid_constant__ CUtensorMap cmap, TcGemmArgs g) {
+  constexpr int BF16 = EPI != kTcEpiF32;
+  constexpr int kStageBytes = STREAMB ? kTcSliceA + kTcSliceB : kTcSliceA;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   __shared__ __align__(8) unsigned long long full_bar[kTcStages], empty_bar[kTcStages];
   __shared__ __align__(8) unsigned long long b_bar, accf_bar[2], acce_bar[2];
@@ -131,13 +151,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ float sbias[kTcBN];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* base = (unsigned char*)(((size_t)tc_smem + 1023) & ~(size_t)1023);
-  const int nkb = g.K / kTcBK;                       // K slices per tile
-  unsigned char* sB = base;                          // nkb x [256][64]
-  unsigned char* sA = base + nkb * kTcSliceB;        // ring of [128][64]
-  unsigned char* sC = sA + kTcStages * kTcSliceA;    // 4 warps x 2 staging buffers
+  const int KS = g.ksplit > 1 ? g.ksplit : 1;
+  const int nkb = g.K / kTcBK / KS;                  // K slices per tile of this CTA
+  // resident B: nkb x [256][64], then the ring of [128][64] A slices;
+  // streamed B: the ring of ([128][64] A, [256][64] B) stages
+  unsigned char* sB = base;
+  unsigned char* sA = STREAMB ? base : base + nkb * kTcSliceB;
+  unsigned char* sC = sA + kTcStages * kStageBytes;  // 4 warps x 2 staging buffers
   const int NT = g.N / kTcBN, MT = g.M / kTcBM;
-  const int groups = gridDim.x / NT;                 // CTAs per column tile
-  const int nt = blockIdx.x % NT, m_first = blockIdx.x / NT;
+  const int groups = gridDim.x / (NT * KS);          // CTAs per (column tile, K range)
+  const int nt = blockIdx.x % NT, ks = (blockIdx.x / NT) % KS, m_first = blockIdx.x / (NT * KS);
+  const int kb0 = ks * nkb;                          // first K slice of this CTA
   const int my_tiles = (m_first < MT) ? (MT - m_first + groups - 1) / groups : 0;
 
   if (threadIdx.x == 0) {
@@ -168,9 +192,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (lane == 0) {
       bool ok = true;
       const unsigned bb = tc_smem_u32(&b_bar);
-      tc_expect_tx(bb, (unsigned)(nkb * kTcSliceB));
-      for (int kb = 0; kb < nkb; ++kb)
-        tc_tma_load(tc_smem_u32(sB + kb * kTcSliceB), &bmap, kb * kTcBK, nt * kTcBN, bb);
+      if (STREAMB) {
+        tc_arrive(bb);                               // nothing resident to wait for
+      } else {
+        tc_expect_tx(bb, (unsigned)(nkb * kTcSliceB));
+        for (int kb = 0; kb < nkb; ++kb)
+          tc_tma_load(tc_smem_u32(sB + kb * kTcSliceB), &bmap, (kb0 + kb) * kTcBK, nt * kTcBN, bb);
+      }
       unsigned u = 0;                                // slices issued
       for (int t = 0; t < my_tiles && ok; ++t) {
         const int mt = m_first + t * groups;
@@ -182,8 +210,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             break;
           }
           const unsigned fb = tc_smem_u32(&full_bar[s]);
-          tc_expect_tx(fb, (unsigned)kTcSliceA);
-          tc_tma_load(tc_smem_u32(sA + s * kTcSliceA), &amap, kb * kTcBK, mt * kTcBM, fb);
+          unsigned char* stg = sA + s * kStageBytes;
+          tc_expect_tx(fb, (unsigned)kStageBytes);
+          tc_tma_load(tc_smem_u32(stg), &amap, (kb0 + kb) * kTcBK, mt * kTcBM, fb);
+          if (STREAMB)
+            tc_tma_load(tc_smem_u32(stg + kTcSliceA), &bmap, (kb0 + kb) * kTcBK, nt * kTcBN, fb);
         }
       }
       if (!ok) atomicOr(g.err, 1u);
@@ -218,8 +249,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const unsigned a0 = tc_smem_u32(sA + s * kTcSliceA);
-          const unsigned b0 = tc_smem_u32(sB + kb * kTcSliceB);
+          const unsigned a0 = tc_smem_u32(sA + s * kStageBytes);
+          const unsigned b0 =
+              STREAMB ? a0 + (unsigned)kTcSliceA : tc_smem_u32(sB + kb * kTcSliceB);
 #pragma unroll
           for (int kk = 0; kk < kTcBK / 16; ++kk) {
             // K = 16 bf16 = 32 bytes further along the swizzled 128-byte rows
@@ -268,6 +300,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
       const int n0 = nt * kTcBN, row0 = mt * kTcBM + q * 32;
+      const int crow0 = ks * g.M + row0;             // a K split's partial goes to its own rows
 #pragma unroll 1
       for (int c0 = 0; c0 < kTcBN; c0 += kCols, ++slab) {
         // the staging buffer of two slabs ago must have been read out
@@ -290,16 +323,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 "=r"(v[h * 16 + 14]), "=r"(v[h * 16 + 15])
               : "r"(taddr));
         }
+        // mask epilogue: this row's 64 auxiliary bf16 values of the slab
+        uint4 ax[EPI == kTcEpiMaskBf16 ? 8 : 1];
+        if constexpr (EPI == kTcEpiMaskBf16) {
+          const uint4* ap = (const uint4*)(g.aux + (size_t)(row0 + lane) * g.ldaux + n0 + c0);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) ax[c] = __ldg(ap + c);
+        }
         asm volatile("tcgen05.wait::ld.sync.aligned;");
         unsigned w[32];                              // this row's 128 bytes of the slab
 #pragma unroll
         for (int i = 0; i < kCols; ++i) {
-          const float f = __uint_as_float(v[i]) + sbias[c0 + i];
-          if constexpr (BF16) {
-            const unsigned b16 = __bfloat16_as_ushort(__float2bfloat16_rn(fmaxf(f, 0.f)));
+          if constexpr (EPI == kTcEpiMaskBf16) {
+            const unsigned word = (&ax[i / 8].x)[(i / 2) & 3];
+            const short h = (short)((i & 1) ? (word >> 16) : (word & 0xFFFFu));
+            const float f = h > 0 ? __uint_as_float(v[i]) : 0.f;    // aux > 0 (bf16 bits)
+            const unsigned b16 = __bfloat16_as_ushort(__float2bfloat16_rn(f));
+            if (i & 1) w[i / 2] |= b16 << 16;
+            else       w[i / 2] = b16;
+          } else if constexpr (BF16) {
+            float f = __uint_as_float(v[i]) + sbias[c0 + i];
+            if constexpr (EPI == kTcEpiReluBf16) f = fmaxf(f, 0.f);
+            const unsigned b16 = __bfloat16_as_ushort(__float2bfloat16_rn(f));
             if (i & 1) w[i / 2] |= b16 << 16;
             else       w[i / 2] = b16;
           } else {
+            const float f = __uint_as_float(v[i]) + sbias[c0 + i];
             w[i] = __float_as_uint(f);
           }
         }
@@ -315,7 +364,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        if (lane == 0) tc_tma_store(&cmap, tc_smem_u32(st), n0 + c0, row0);
+        if (lane == 0) tc_tma_store(&cmap, tc_smem_u32(st), n0 + c0, crow0);
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       tc_arrive(tc_smem_u32(&acce_bar[acc]));

@@ -175,7 +175,9 @@ struct Plan {
   int variant, n, delta, m, U, nprimes, block_threads, grid, arith;
   int symmetry;     // SK_SYMMETRY_* used
   int sign;         // Lemma 2.4 sign s (+1 / -1) when symmetry uses it
-  int fixed_bit;    // free bit held at +1 by Lemma 2.4 (0: none)
+  int fixed_bit;    // free bit held at +1 by Lemma 2.4, or an extended
+                    // sequence's hole (0: none); item indices skip it
+  int hole;         // extended Skolem sequences: the hole position (0: none)
   unsigned long long pres, items;
   uint64_t primes[kMaxPrimes];
   Primes P;
@@ -183,10 +185,29 @@ struct Plan {
 };
 
 static int make_plan(int variant, int n, const sk_count_opts* o, Plan* pl,
-                     int method = kMethodAlgebraic) {
+                     int method = kMethodAlgebraic, int hole = 0) {
   if (variant < SK_SKOLEM || variant > SK_HOOKED || n < 1 || n > kMaxN) return SK_EINVAL;
+  // Extended Skolem sequences (Sec. 1.2; one hole in 1..2n+1, d_k = k):
+  // holes 1 and 2n+1 leave the Skolem problem, 2 and 2n the hooked one.  Any
+  // other hole is mirrored into the upper half (reversal maps the sequences
+  // of hole h onto those of hole 2n+2-h), left out of the position mask, and
+  // skipped by the item index like Lemma 2.4's fixed variable -- so it must
+  // lie above the walk (bit >= walk width >= the unrolled inner width).
+  int hole_bit = -1;
+  if (hole) {
+    if (method != kMethodAlgebraic || variant != SK_SKOLEM || hole < 1 || hole > 2 * n + 1)
+      return SK_EINVAL;
+    if (o && o->symmetry != SK_SYMMETRY_NEGATION) return SK_EINVAL;
+    if (hole == 2 || hole == 2 * n) {
+      variant = SK_HOOKED;
+    } else if (hole != 1 && hole != 2 * n + 1) {
+      variant = SK_HOOKED;                     // d_k = k over the span 1..2n+1
+      hole_bit = std::max(hole, 2 * n + 2 - hole) - 1;
+    }
+  }
   std::memset(pl, 0, sizeof(*pl));
   pl->method = method;
+  pl->hole = hole;
   if (method == kMethodInclusionExclusion) {
     // the same walk over all 2n variables of P: no symmetry, exact-digit form
     if (n > kMaxIeN) return SK_EINVAL;
@@ -211,6 +232,7 @@ static int make_plan(int variant, int n, const sk_count_opts* o, Plan* pl,
     if (pl->m > mmax) pl->m = mmax;
   }
   pl->pres = position_mask(variant, n);
+  if (hole_bit >= 0) pl->pres = ((1ULL << (2 * n + 1)) - 1ULL) & ~(1ULL << hole_bit);
   // Lemma 2.4: negating the even positions multiplies the summand by
   // s = (-1)^{#even positions in P + #odd d_k}.  With s = +1 the summand is
   // constant on {X, X with the odd (Skolem, Langford) or even (hooked; its
@@ -219,15 +241,29 @@ static int make_plan(int variant, int n, const sk_count_opts* o, Plan* pl,
   // doubled; with s = -1 the sum is 0.
   const int sym = o ? o->symmetry : SK_SYMMETRY_NEGATION;
   if (sym != SK_SYMMETRY_NEGATION && sym != SK_SYMMETRY_NEGATION_EVEN &&
-      sym != SK_SYMMETRY_REVERSAL)
+      sym != SK_SYMMETRY_REVERSAL && sym != SK_SYMMETRY_REVERSAL_EVEN)
     return SK_EINVAL;
-  if (sym == SK_SYMMETRY_REVERSAL && (variant == SK_HOOKED || pl->arith != SK_ARITH_LIMBS))
+  const bool reversal = sym == SK_SYMMETRY_REVERSAL || sym == SK_SYMMETRY_REVERSAL_EVEN;
+  if (reversal && (variant == SK_HOOKED || pl->arith != SK_ARITH_LIMBS))
     return SK_EINVAL;                     // hooked Skolem's P is not reversal-symmetric
   pl->symmetry = SK_SYMMETRY_NEGATION;
   pl->sign = 1;
   pl->fixed_bit = 0;
   int Feff = F;
-  if (sym == SK_SYMMETRY_NEGATION_EVEN && n >= 4) {
+  // Lemmas 2.3 and 2.4 together need the mirrored walk (n >= kMirrorMinN);
+  // below it, Lemma 2.4 alone
+  const bool even_only = sym == SK_SYMMETRY_NEGATION_EVEN ||
+                         (sym == SK_SYMMETRY_REVERSAL_EVEN && n < kMirrorMinN);
+  if (sym == SK_SYMMETRY_REVERSAL_EVEN && n >= kMirrorMinN) {
+    // the sign of Lemma 2.4 decides the zero classes; the mirrored items
+    // below carry the rest
+    int e = 0, odd_d = 0;
+    for (int i = 0; i < 64; ++i)
+      if (((pl->pres >> i) & 1ULL) && (i & 1)) ++e;
+    for (int k = 1; k <= n; ++k) odd_d += (k + pl->delta) & 1;
+    pl->sign = ((e + odd_d) & 1) ? -1 : 1;
+  }
+  if (even_only && n >= 4) {
     int e = 0, odd_d = 0;
     for (int i = 0; i < 64; ++i)
       if (((pl->pres >> i) & 1ULL) && (i & 1)) ++e;     // bit i = position i+1
@@ -239,13 +275,18 @@ static int make_plan(int variant, int n, const sk_count_opts* o, Plan* pl,
     if (!(o && o->walk_bits) && pl->m > pl->fixed_bit) pl->m = pl->fixed_bit;
     if (pl->m > pl->fixed_bit) return SK_EINVAL;        // the fixed bit must lie above the walk
   }
+  if (hole_bit >= 0) {
+    pl->fixed_bit = hole_bit;
+    if (!(o && o->walk_bits) && pl->m > hole_bit) pl->m = hole_bit;
+    if (pl->m > hole_bit) return SK_EINVAL;             // the hole must lie above the walk
+  }
   if (pl->m < pl->U || pl->m > F || pl->m > mmax || F - pl->m > 56) return SK_EINVAL;
   if (method == kMethodInclusionExclusion) Feff = F + 1;   // max P is a variable too
   pl->items = 1ULL << (Feff - pl->m);
   // Lemma 2.3 (reversal): the mirrored walk over bits 1..h and their mirror
   // images, items = x_1 and the middle bits, one of each pair of mirror-image
   // items enumerated with weight 2 (sk_mirror.cuh)
-  if (sym == SK_SYMMETRY_REVERSAL && n >= kMirrorMinN) {
+  if (reversal && n >= kMirrorMinN) {
     int m = pl->m;
     if (!(o && o->walk_bits)) {
       const int cap = std::min(mmax, 2 * n - 2) & ~1;
@@ -255,14 +296,22 @@ static int make_plan(int variant, int n, const sk_count_opts* o, Plan* pl,
     }
     if ((m & 1) || m / 2 < pl->U || m > 2 * n - 2 || m > mmax) return SK_EINVAL;
     pl->m = m;
-    pl->symmetry = SK_SYMMETRY_REVERSAL;
-    pl->items = 2 * mirror_shape(n, m / 2).per_side;
+    pl->symmetry = sym;
+    // Lemma 2.4 in the existence classes: negating the odd positions keeps
+    // the summand, flips x_1 and keeps x_2n, and maps the mirrored walk's
+    // positions onto themselves, so it carries every item with x_1 = +1
+    // onto one with x_1 = -1 of equal sum: the x_1 = +1 side alone (items
+    // 0 .. per_side-1), doubled on the host
+    const unsigned long long per_side = mirror_shape(n, m / 2).per_side;
+    pl->items = sym == SK_SYMMETRY_REVERSAL_EVEN ? per_side : 2 * per_side;
   }
   pl->block_threads = (o && o->block_threads) ? o->block_threads : 256;
   if (pl->block_threads < 32 || pl->block_threads > 256 || (pl->block_threads & 31)) return SK_EINVAL;
   pl->grid = (o && o->grid > 0) ? o->grid : 0;
+  const bool mirrored =
+      pl->symmetry == SK_SYMMETRY_REVERSAL || pl->symmetry == SK_SYMMETRY_REVERSAL_EVEN;
   pl->fn = method == kMethodInclusionExclusion     ? ie_launcher(pl->delta, n)
-           : pl->symmetry == SK_SYMMETRY_REVERSAL ? mirror_launcher(pl->delta, n)
+           : mirrored                              ? mirror_launcher(pl->delta, n)
            : pl->arith == SK_ARITH_LIMBS          ? limb_launcher(pl->delta, n)
                                                   : exact_launcher(pl->delta, n, pl->nprimes);
   if (!pl->fn) return SK_EINVAL;
@@ -342,7 +391,9 @@ static std::string ckpt_header(const Plan& pl, unsigned long long chunk_items,
   std::string h(buf);
   if (pl.symmetry == SK_SYMMETRY_NEGATION_EVEN) h += " s=lemma2.4";
   if (pl.symmetry == SK_SYMMETRY_REVERSAL) h += " s=lemma2.3";
+  if (pl.symmetry == SK_SYMMETRY_REVERSAL_EVEN) h += " s=lemma2.3+2.4";
   if (pl.method == kMethodInclusionExclusion) h += " method=inclusion-exclusion";
+  if (pl.hole) h += " hole=" + std::to_string(pl.hole);
   return h;
 }
 
@@ -496,11 +547,26 @@ int finalize_count(int variant, int n, int convention, int nprimes, const uint64
   return apply_convention(variant, n, convention, coeff, out);
 }
 
+// Output convention of an extended sequence count: reversal maps hole h to
+// hole 2n+2-h, so reflections are identified only where it maps the position
+// set onto itself -- holes 1 and 2n+1 (the Skolem problem) and n+1 (Rosa's:
+// no sequence is its own reflection, the pair of 1s cannot be symmetric about
+// n+1) -- and the count of any other hole is returned as it is.
+static int apply_convention_hole(int n, int hole, int convention, sk_u128 coeff, sk_u128* out) {
+  if (hole == 1 || hole == 2 * n + 1) return apply_convention(SK_SKOLEM, n, convention, coeff, out);
+  if (hole == n + 1 && convention == SK_COUNT_REFLECTIONS_IDENTIFIED) {
+    if (coeff.lo & 1) return SK_EMISMATCH;
+    u128_half(&coeff);
+  }
+  *out = coeff;
+  return SK_OK;
+}
+
 int count_impl(int variant, int n, const sk_count_opts* o, sk_u128* out, sk_count_report* rep,
-               int method = kMethodAlgebraic) {
+               int method = kMethodAlgebraic, int hole = 0) {
   auto t0 = std::chrono::steady_clock::now();
   Plan pl;
-  int st = make_plan(variant, n, o, &pl, method);
+  int st = make_plan(variant, n, o, &pl, method, hole);
   if (st) return st;
   if (o && o->convention != SK_COUNT_REFLECTIONS_IDENTIFIED && o->convention != SK_COUNT_ALL)
     return SK_EINVAL;
@@ -590,7 +656,8 @@ int count_impl(int variant, int n, const sk_count_opts* o, sk_u128* out, sk_coun
   if (st) return st;
   const bool complete = done_total == nchunks;
   unmont(pl, H);
-  if (pl.symmetry == SK_SYMMETRY_NEGATION_EVEN)      // Lemma 2.4, s = +1: H = 2 H'
+  if (pl.symmetry == SK_SYMMETRY_NEGATION_EVEN ||     // Lemma 2.4, s = +1: H = 2 H'
+      pl.symmetry == SK_SYMMETRY_REVERSAL_EVEN)
     for (int i = 0; i < pl.nprimes; ++i) H[i] = (H[i] * 2) % pl.primes[i];
   sk_u128 coeff = {0, 0};
   if (complete) {
@@ -624,7 +691,9 @@ int count_impl(int variant, int n, const sk_count_opts* o, sk_u128* out, sk_coun
   }
   if (!complete) return SK_OK;
   sk_u128 v;
-  st = apply_convention(variant, n, o ? o->convention : SK_COUNT_REFLECTIONS_IDENTIFIED, coeff, &v);
+  const int conv = o ? o->convention : SK_COUNT_REFLECTIONS_IDENTIFIED;
+  st = pl.hole ? apply_convention_hole(n, pl.hole, conv, coeff, &v)
+               : apply_convention(variant, n, conv, coeff, &v);
   if (st) return st;
   if (out) *out = v;
   return SK_OK;
@@ -632,7 +701,10 @@ int count_impl(int variant, int n, const sk_count_opts* o, sk_u128* out, sk_coun
 
 int item_residues_impl(int variant, int n, int m, uint64_t q_lo, uint64_t count, int nprimes,
                        const uint64_t* primes, int arith, uint64_t* out,
-                       int method = kMethodAlgebraic) {
+                       int method = kMethodAlgebraic, int hole = 0) {
+  // items of an extended sequence's own position set: holes n+1..2n+1 (a
+  // lower hole would be counted on its mirror image)
+  if (hole && hole < n + 1) return SK_EINVAL;
   if (!out || !primes || count == 0 || count > (1ULL << 20)) return SK_EINVAL;
   sk_count_opts o;
   std::memset(&o, 0, sizeof(o));
@@ -641,7 +713,7 @@ int item_residues_impl(int variant, int n, int m, uint64_t q_lo, uint64_t count,
   for (int i = 0; i < nprimes && i < SK_MAX_PRIMES; ++i) o.primes[i] = primes[i];
   o.walk_bits = m;
   Plan pl;
-  int st = make_plan(variant, n, &o, &pl, method);
+  int st = make_plan(variant, n, &o, &pl, method, hole);
   if (st) return st;
   if (q_lo >= pl.items || count > pl.items - q_lo) return SK_EINVAL;
   st = check_device();
@@ -747,4 +819,17 @@ extern "C" int sk_ie_item_residues(int variant, int n, int m, uint64_t q_lo, uin
                                    int nprimes, const uint64_t* primes, uint64_t* out) {
   return sk::item_residues_impl(variant, n, m, q_lo, count, nprimes, primes, SK_ARITH_LIMBS, out,
                                 sk::kMethodInclusionExclusion);
+}
+
+extern "C" int sk_count_extended(int n, int hole, const sk_count_opts* opts, sk_u128* out,
+                                 sk_count_report* rep) {
+  if (hole < 1 || hole > 2 * n + 1) return SK_EINVAL;    // (hole 0 would mean "no hole")
+  return sk::count_impl(SK_SKOLEM, n, opts, out, rep, sk::kMethodAlgebraic, hole);
+}
+
+extern "C" int sk_extended_item_residues(int n, int hole, int m, uint64_t q_lo, uint64_t count,
+                                         int nprimes, const uint64_t* primes, uint64_t* out) {
+  if (hole < 1 || hole > 2 * n + 1) return SK_EINVAL;
+  return sk::item_residues_impl(SK_SKOLEM, n, m, q_lo, count, nprimes, primes, SK_ARITH_LIMBS, out,
+                                sk::kMethodAlgebraic, hole);
 }

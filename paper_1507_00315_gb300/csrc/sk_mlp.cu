@@ -62,16 +62,27 @@ __global__ void __launch_bounds__(256) mlp_inputs_kernel(const unsigned char* __
   }
 }
 
-// out[c] += sum over rows of in[r][c] (bias gradients).
-__global__ void colsum_kernel(const __nv_bfloat16* __restrict__ in, int rows, int cols,
-                              int rows_per_block, float* out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cols) return;
-  const int r0 = blockIdx.y * rows_per_block;
-  const int r1 = min(rows, r0 + rows_per_block);
-  float acc = 0.f;
-  for (int r = r0; r < r1; ++r) acc += __bfloat162float(in[(size_t)r * cols + c]);
-  atomicAdd(&out[c], acc);
+// Bias gradients: column sums of a [rows][cols] bf16 matrix in two passes of
+// fixed order (the same bits every call).  Pass 1: block (x, y) sums rows
+// y*kColRows .. of 32 columns, 8 row phases per column (a warp reads 32
+// adjacent columns of one row), then the phases in order in shared memory,
+// into part[y][c].  Pass 2 (splitk_sum_kernel) adds the parts in order y.
+constexpr int kColRows = 128;
+__global__ void colsum_part_kernel(const __nv_bfloat16* __restrict__ in, int rows, int cols,
+                                   float* __restrict__ part) {
+  __shared__ float s[8][33];
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  const int r0 = blockIdx.y * kColRows, r1 = min(rows, r0 + kColRows);
+  float a = 0.f;
+  if (c < cols)
+    for (int r = r0 + threadIdx.y; r < r1; r += 8) a += __bfloat162float(in[(size_t)r * cols + c]);
+  s[threadIdx.y][threadIdx.x] = a;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < cols) {
+    float t = 0.f;
+    for (int i = 0; i < 8; ++i) t += s[i][threadIdx.x];
+    part[(size_t)blockIdx.y * cols + c] = t;
+  }
 }
 
 // Adam (Kingma & Ba 2015) over the flat parameter vector; refreshes the bf16
@@ -176,29 +187,83 @@ MoveTable move_table(const Mlp& m) {
   return t;
 }
 
-// out[c][r] = in[r][c] for a rows x cols bf16 matrix.
-__global__ void transpose_bf16_kernel(const __nv_bfloat16* in, int rows, int cols,
-                                      __nv_bfloat16* out) {
-  __shared__ __nv_bfloat16 t[32][33];
-  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int r = r0 + i, c = c0 + threadIdx.x;
-    if (r < rows && c < cols) t[i][threadIdx.x] = in[(size_t)r * cols + c];
+// Up to three transposes in one launch: out[c][r] = in[r][c] for a
+// [rows][cols] bf16 matrix (rows, cols multiples of 64; blockIdx.z picks the
+// matrix).  64 x 64 tiles move in 16-byte pieces through shared memory (row
+// pitch 66 elements: the 4-byte stores of a warp hit distinct banks).  With
+// part, the tile's column sums over its 64 rows are also written, in a fixed
+// order, to part[r0 / 64][c] (the first pass of a bias gradient).
+struct TransposeJob {
+  const __nv_bfloat16* in;
+  __nv_bfloat16* out;
+  float* part;
+  int rows, cols;
+};
+struct TransposeJobs {
+  TransposeJob j[3];
+};
+
+__global__ void __launch_bounds__(256) transpose_set_kernel(TransposeJobs jobs) {
+  __shared__ __align__(16) __nv_bfloat16 t[64][66];
+  // this block's matrix, chosen field by field (a dynamic index into the
+  // parameter array would copy it to local memory)
+  const int z = blockIdx.z;
+  TransposeJob J;
+  J.in = z == 0 ? jobs.j[0].in : (z == 1 ? jobs.j[1].in : jobs.j[2].in);
+  J.out = z == 0 ? jobs.j[0].out : (z == 1 ? jobs.j[1].out : jobs.j[2].out);
+  J.part = z == 0 ? jobs.j[0].part : (z == 1 ? jobs.j[1].part : jobs.j[2].part);
+  J.rows = z == 0 ? jobs.j[0].rows : (z == 1 ? jobs.j[1].rows : jobs.j[2].rows);
+  J.cols = z == 0 ? jobs.j[0].cols : (z == 1 ? jobs.j[1].cols : jobs.j[2].cols);
+  const int c0 = blockIdx.x * 64, r0 = blockIdx.y * 64;
+  if (c0 >= J.cols || r0 >= J.rows) return;          // a smaller matrix's spare blocks
+  for (int q = threadIdx.x; q < 512; q += 256) {
+    const int i = q >> 3, c8 = (q & 7) * 8;
+    const uint4 v = *(const uint4*)(J.in + (size_t)(r0 + i) * J.cols + c0 + c8);
+    unsigned* dst = (unsigned*)&t[i][c8];
+    dst[0] = v.x;
+    dst[1] = v.y;
+    dst[2] = v.z;
+    dst[3] = v.w;
   }
   __syncthreads();
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int c = c0 + i, r = r0 + threadIdx.x;
-    if (r < rows && c < cols) out[(size_t)c * rows + r] = t[threadIdx.x][i];
+  for (int q = threadIdx.x; q < 512; q += 256) {
+    const int o = q >> 3, r8 = (q & 7) * 8;          // output row c0 + o, columns r0 + r8 ..
+    unsigned w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      w[k] = (unsigned)__bfloat16_as_ushort(t[r8 + 2 * k][o]) |
+             ((unsigned)__bfloat16_as_ushort(t[r8 + 2 * k + 1][o]) << 16);
+    *(uint4*)(J.out + (size_t)(c0 + o) * J.rows + r0 + r8) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  if (J.part && threadIdx.x < 64) {
+    float a = 0.f;
+    for (int i = 0; i < 64; ++i) a += __bfloat162float(t[i][threadIdx.x]);
+    J.part[(size_t)blockIdx.y * J.cols + c0 + threadIdx.x] = a;
   }
 }
 
-cudaError_t refresh_transposed(Mlp& m, cudaStream_t s) {
-  dim3 b(32, 8);
-  transpose_bf16_kernel<<<dim3(kHidden / 32, m.K1 / 32), b, 0, s>>>(m.W1, m.K1, kHidden, m.W1t);
-  transpose_bf16_kernel<<<dim3(kHidden / 32, kHidden / 32), b, 0, s>>>(m.W2, kHidden, kHidden, m.W2t);
-  transpose_bf16_kernel<<<dim3(m.NMp / 32, kHidden / 32), b, 0, s>>>(m.W3, kHidden, m.NMp, m.W3t);
-  m.wt_dirty = 0;
+static cudaError_t transpose_set(const TransposeJob* jobs, int count, cudaStream_t s) {
+  TransposeJobs J;
+  std::memset(&J, 0, sizeof(J));
+  int gx = 1, gy = 1;
+  for (int i = 0; i < count; ++i) {
+    if (jobs[i].rows % 64 || jobs[i].cols % 64) return cudaErrorInvalidValue;
+    J.j[i] = jobs[i];
+    gx = std::max(gx, jobs[i].cols / 64);
+    gy = std::max(gy, jobs[i].rows / 64);
+  }
+  transpose_set_kernel<<<dim3(gx, gy, count), 256, 0, s>>>(J);
   return cudaGetLastError();
+}
+
+// The K-major (transposed) bf16 weights of the tcgen05 forward, one launch.
+cudaError_t refresh_transposed(Mlp& m, cudaStream_t s) {
+  const TransposeJob jobs[3] = {{m.W1, m.W1t, nullptr, m.K1, kHidden},
+                                {m.W2, m.W2t, nullptr, kHidden, kHidden},
+                                {m.W3, m.W3t, nullptr, kHidden, m.NMp}};
+  cudaError_t e = transpose_set(jobs, 3, s);
+  if (e == cudaSuccess) m.wt_dirty = 0;
+  return e;
 }
 
 // The driver's tensor-map encoder, found through the runtime (no link
@@ -241,16 +306,19 @@ static bool make_tc_maps(Mlp& m) {
          encode_map(&m.tmB[2], m.W3t, 2, m.NMp, kHidden, kTcBN) &&
          encode_map(&m.tmC[0], m.H1, 2, m.max_batch, kHidden, 32) &&
          encode_map(&m.tmC[1], m.H2, 2, m.max_batch, kHidden, 32) &&
-         encode_map(&m.tmC[2], m.Z, 4, m.max_batch, m.NMp, 32);
+         encode_map(&m.tmC[2], m.Z, 4, m.max_batch, m.NMp, 32) &&
+         encode_map(&m.tmZb, m.Z, 2, m.max_batch, m.NMp, 32) &&
+         encode_map(&m.tmBA[0], m.dZ, 2, m.max_batch, m.NMp, kTcBM) &&
+         encode_map(&m.tmBA[1], m.dH2, 2, m.max_batch, kHidden, kTcBM) &&
+         encode_map(&m.tmBB[0], m.W3, 2, kHidden, m.NMp, kTcBN) &&
+         encode_map(&m.tmBB[1], m.W2, 2, kHidden, kHidden, kTcBN) &&
+         encode_map(&m.tmBC[0], m.dH2, 2, m.max_batch, kHidden, 32) &&
+         encode_map(&m.tmBC[1], m.dH1, 2, m.max_batch, kHidden, 32);
 }
 
-// C = A B^T + bias on tcgen05: bf16 = 1 writes bf16(relu(.)), 0 writes fp32.
-cudaError_t gemm_tc(const TcGemmArgs& g, const CUtensorMap& amap, const CUtensorMap& bmap,
-                    const CUtensorMap& cmap, int bf16, cudaStream_t s) {
-  if (g.M % kTcBM || g.N % kTcBN || g.K % kTcBK || g.K > kTcMaxK || g.M <= 0)
-    return cudaErrorInvalidValue;
-  // the shared-memory opt-in is a per-device function attribute: set it once
-  // per device, with that device current
+// The shared-memory opt-in is a per-device function attribute: set it once
+// per device, with that device current, for every instantiation used.
+static cudaError_t tc_attributes(int* dev_out) {
   int dev = 0;
   cudaError_t e0 = cudaGetDevice(&dev);
   if (e0 != cudaSuccess) return e0;
@@ -258,30 +326,55 @@ cudaError_t gemm_tc(const TcGemmArgs& g, const CUtensorMap& amap, const CUtensor
   static std::once_flag once[kMaxDevices];
   static cudaError_t attr_err[kMaxDevices];
   std::call_once(once[dev], [dev]() {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<1>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<kTcEpiReluBf16, false>, at, kTcSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_tc_kernel<kTcEpiF32, false>, at, kTcSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_tc_kernel<kTcEpiBf16, false>, at, kTcSmem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gemm_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               kTcSmem);
+      e = cudaFuncSetAttribute(gemm_tc_kernel<kTcEpiMaskBf16, true>, at, kTcSmemStream);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(gemm_tc_kernel<kTcEpiF32, true>, at, kTcSmemStream);
     attr_err[dev] = e;
   });
-  if (attr_err[dev] != cudaSuccess) return attr_err[dev];
+  *dev_out = dev;
+  return attr_err[dev];
+}
+
+// C = A B^T on tcgen05 (epilogue EPI; STREAMB: B streamed through the ring,
+// any K; a K split of g.ksplit ranges writes its partials to rows ks * M..).
+// Grid: one CTA per SM, a whole number of CTAs per (column tile, K range).
+template <int EPI, bool STREAMB>
+cudaError_t gemm_tc_launch(const TcGemmArgs& g, const CUtensorMap& amap, const CUtensorMap& bmap,
+                           const CUtensorMap& cmap, cudaStream_t s) {
+  const int KS = g.ksplit > 1 ? g.ksplit : 1;
+  if (g.M <= 0 || g.K <= 0 || g.M % kTcBM || g.N % kTcBN || g.K % (kTcBK * KS))
+    return cudaErrorInvalidValue;
+  if (!STREAMB && (g.K > kTcMaxK || KS > 1)) return cudaErrorInvalidValue;
+  if (EPI == kTcEpiMaskBf16 && (!g.aux || g.ldaux % 8)) return cudaErrorInvalidValue;
+  int dev = 0;
+  cudaError_t e = tc_attributes(&dev);
+  if (e != cudaSuccess) return e;
   const int sms = device_sm_count(dev);
-  // one CTA per SM, a whole number of CTAs per 256-wide column tile
   const int NT = g.N / kTcBN, MT = g.M / kTcBM;
-  int per = sms / NT;
+  int per = sms / (NT * KS);
   if (per < 1) per = 1;
   if (per > MT) per = MT;
-  if (bf16)
-    gemm_tc_kernel<1><<<per * NT, kTcThreads, kTcSmem, s>>>(amap, bmap, cmap, g);
-  else
-    gemm_tc_kernel<0><<<per * NT, kTcThreads, kTcSmem, s>>>(amap, bmap, cmap, g);
+  gemm_tc_kernel<EPI, STREAMB><<<per * NT * KS, kTcThreads, STREAMB ? kTcSmemStream : kTcSmem, s>>>(
+      amap, bmap, cmap, g);
   return cudaGetLastError();
 }
 
+// The forward's layers: epi = kTcEpiReluBf16 (hidden layers), kTcEpiF32 or
+// kTcEpiBf16 (logits).
+cudaError_t gemm_tc(const TcGemmArgs& g, const CUtensorMap& amap, const CUtensorMap& bmap,
+                    const CUtensorMap& cmap, int epi, cudaStream_t s) {
+  if (epi == kTcEpiReluBf16) return gemm_tc_launch<kTcEpiReluBf16, false>(g, amap, bmap, cmap, s);
+  if (epi == kTcEpiBf16) return gemm_tc_launch<kTcEpiBf16, false>(g, amap, bmap, cmap, s);
+  return gemm_tc_launch<kTcEpiF32, false>(g, amap, bmap, cmap, s);
+}
+
 // Forward pass for B (multiple of 128) states whose slots are already in
-// m.slots: X, H1, H2 (bf16) and Z (fp32 logits).
-cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s) {
+// m.slots: X, H1, H2 (bf16) and Z (fp32 logits, or bf16 with logits_bf16).
+cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s, bool logits_bf16) {
   mlp_inputs_kernel<<<(B + 7) / 8, 256, 0, s>>>(m.slots, B, m.n, m.delta, m.K1, m.X);
   if (m.use_tc) {
     cudaError_t e = cudaSuccess;
@@ -290,13 +383,14 @@ cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s) {
     TcGemmArgs t;
     std::memset(&t, 0, sizeof(t));
     t.M = B; t.N = kHidden; t.K = m.K1; t.bias = m.b1; t.err = m.tc_err;
-    e = gemm_tc(t, m.tmA[0], m.tmB[0], m.tmC[0], 1, s);
+    e = gemm_tc(t, m.tmA[0], m.tmB[0], m.tmC[0], kTcEpiReluBf16, s);
     if (e != cudaSuccess) return e;
     t.K = kHidden; t.bias = m.b2;
-    e = gemm_tc(t, m.tmA[1], m.tmB[1], m.tmC[1], 1, s);
+    e = gemm_tc(t, m.tmA[1], m.tmB[1], m.tmC[1], kTcEpiReluBf16, s);
     if (e != cudaSuccess) return e;
     t.N = m.NMp; t.bias = m.b3;
-    return gemm_tc(t, m.tmA[2], m.tmB[2], m.tmC[2], 0, s);
+    return logits_bf16 ? gemm_tc(t, m.tmA[2], m.tmB[2], m.tmZb, kTcEpiBf16, s)
+                       : gemm_tc(t, m.tmA[2], m.tmB[2], m.tmC[2], kTcEpiF32, s);
   }
   GemmArgs g;
   std::memset(&g, 0, sizeof(g));
@@ -308,7 +402,111 @@ cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s) {
   e = gemm<false, false, EPI_BF16_RELU>(g, 1, s);
   if (e != cudaSuccess) return e;
   g.N = m.NMp; g.A = m.H2; g.B = m.W3; g.ldb = m.NMp; g.C = m.Z; g.ldc = m.NMp; g.bias = m.b3;
-  return gemm<false, false, EPI_F32>(g, 1, s);
+  return logits_bf16 ? gemm<false, false, EPI_BF16>(g, 1, s) : gemm<false, false, EPI_F32>(g, 1, s);
+}
+
+// out[i] = sum over ks of ws[ks][i], in the order ks = 0, 1, ... (the K
+// split's partial products, summed the same way every call).
+__global__ void splitk_sum_kernel(const float* __restrict__ ws, int KS, size_t count,
+                                  float* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x) {
+    float a = 0.f;
+    for (int k = 0; k < KS; ++k) a += ws[(size_t)k * count + i];
+    out[i] = a;
+  }
+}
+
+// K ranges of a weight-gradient product: a power of two that divides the K
+// slices, at most 16, aiming at one CTA per SM.
+static int ksplit_for(int tiles, int kslices, int sms) {
+  int ks = 1;
+  while (ks < 16 && tiles * ks * 2 <= sms && kslices % (ks * 2) == 0) ks *= 2;
+  return ks;
+}
+
+// gW[i] = sum over ks of ws[ks][i] (i < MN, the K split's partial products)
+// and gb[c] = sum over p of part[p][c] (c < N, the column sums of the
+// transpose's 64-row tiles), each in a fixed order: the last pass of a weight
+// gradient and of its bias gradient in one launch.
+__global__ void grad_finish_kernel(const float* __restrict__ ws, int KS, size_t MN, float* gW,
+                                   const float* __restrict__ part, int parts, int N, float* gb) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < MN + N;
+       i += (size_t)gridDim.x * blockDim.x) {
+    float a = 0.f;
+    if (i < MN) {
+      for (int k = 0; k < KS; ++k) a += ws[(size_t)k * MN + i];
+      gW[i] = a;
+    } else {
+      const size_t c = i - MN;
+      for (int p = 0; p < parts; ++p) a += part[(size_t)p * N + c];
+      gb[c] = a;
+    }
+  }
+}
+
+// The workspace of the tcgen05 backward for batches up to B: K-major copies
+// TA [256][B] and TB [NMp][B] of the weight-gradient operands, 16 K-split
+// partials of the largest weight gradient, and the bias gradients' column
+// sums of 64-row tiles [B / 64][NMp].  Grown on demand.
+struct BwdSpace {
+  __nv_bfloat16 *TA, *TB;
+  float *WS, *part;
+};
+static cudaError_t bwd_workspace(Mlp& m, int B, BwdSpace* w) {
+  auto a256 = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t wide = m.NMp > kHidden ? m.NMp : kHidden;
+  const size_t ta = a256((size_t)kHidden * B * 2), tb = a256((size_t)m.NMp * B * 2),
+               ws = a256((size_t)16 * kHidden * wide * 4), pt = (size_t)(B / 64) * wide * 4;
+  if (ta + tb + ws + pt > m.bwd_bytes) {
+    if (m.bwd_ws) cudaFree(m.bwd_ws);
+    m.bwd_ws = nullptr;
+    m.bwd_bytes = 0;
+    cudaError_t e = cudaMalloc(&m.bwd_ws, ta + tb + ws + pt);
+    if (e != cudaSuccess) return e;
+    m.bwd_bytes = ta + tb + ws + pt;
+  }
+  char* p = (char*)m.bwd_ws;
+  w->TA = (__nv_bfloat16*)p;
+  w->TB = (__nv_bfloat16*)(p + ta);
+  w->WS = (float*)(p + ta + tb);
+  w->part = (float*)(p + ta + tb + ws);
+  return cudaSuccess;
+}
+
+// One weight gradient gW [M][N] (fp32) = A^T D and its bias gradient gb [N]
+// = the column sums of D, on tcgen05; A [B][M] and D [B][N] bf16 row-major:
+// both transposed to K-major copies in one launch (which also sums D's
+// 64-row tiles), the K = B reduction split over CTAs, then the partials of
+// both summed in a fixed order.
+static cudaError_t weight_grad_tc(Mlp& m, int B, const __nv_bfloat16* A, int M,
+                                  const __nv_bfloat16* D, int N, float* gW, float* gb,
+                                  const BwdSpace& w, int sms, cudaStream_t s) {
+  const TransposeJob jobs[2] = {{A, w.TA, nullptr, B, M}, {D, w.TB, w.part, B, N}};
+  cudaError_t e = transpose_set(jobs, 2, s);
+  if (e != cudaSuccess) return e;
+  const int KS = ksplit_for((M / kTcBM) * (N / kTcBN), B / kTcBK, sms);
+  CUtensorMap am, bm, cm;
+  if (!encode_map(&am, w.TA, 2, M, B, kTcBM) || !encode_map(&bm, w.TB, 2, N, B, kTcBN) ||
+      !encode_map(&cm, w.WS, 4, KS * M, N, 32))
+    return cudaErrorInvalidValue;
+  TcGemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.M = M; g.N = N; g.K = B; g.ksplit = KS; g.err = m.tc_err;
+  e = gemm_tc_launch<kTcEpiF32, true>(g, am, bm, cm, s);
+  if (e != cudaSuccess) return e;
+  const size_t MN = (size_t)M * N;
+  grad_finish_kernel<<<(unsigned)std::min<size_t>((MN + N + 255) / 256, 1024), 256, 0, s>>>(
+      w.WS, KS, MN, gW, w.part, B / 64, N, gb);
+  return cudaGetLastError();
+}
+
+// out[c] = sum over the B rows of in[r][c] (B a multiple of 128), in a fixed order.
+static void colsum(const Mlp& m, const __nv_bfloat16* in, int B, int cols, float* out,
+                   cudaStream_t s) {
+  const int parts = (B + kColRows - 1) / kColRows;
+  colsum_part_kernel<<<dim3((cols + 31) / 32, parts), dim3(32, 8), 0, s>>>(in, B, cols, m.colpart);
+  splitk_sum_kernel<<<(cols + 255) / 256, 256, 0, s>>>(m.colpart, parts, (size_t)cols, out);
 }
 
 int splits_for(int K) {
@@ -317,13 +515,62 @@ int splits_for(int K) {
   return sp;
 }
 
+// The side stream of the tcgen05 backward and its four events, made on first use.
+static cudaError_t side_stream(Mlp& m) {
+  if (m.side) return cudaSuccess;
+  cudaError_t e = cudaStreamCreateWithFlags(&m.side, cudaStreamNonBlocking);
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&m.ev[i], cudaEventDisableTiming);
+  return e;
+}
+
 // Loss and gradients of a batch (after mlp_forward_dev): gW*, gb* (fp32).
-cudaError_t mlp_backward_dev(Mlp& m, int B, float beta_star, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(m.gW1, 0, m.nparams * sizeof(float), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(m.loss, 0, sizeof(float), s);
+// The loss goes to *loss when given (accumulated: the caller zeroes it),
+// else to m.loss (zeroed here).
+cudaError_t mlp_backward_dev(Mlp& m, int B, float beta_star, cudaStream_t s,
+                             float* loss = nullptr) {
+  cudaError_t e = cudaSuccess;
+  if (!m.use_tc) e = cudaMemsetAsync(m.gW1, 0, m.nparams * sizeof(float), s);  // atomics add up
+  if (e == cudaSuccess && !loss) e = cudaMemsetAsync(m.loss, 0, sizeof(float), s);
   if (e != cudaSuccess) return e;
   mlp_loss_kernel<<<(B + 7) / 8, 256, 0, s>>>(m.Z, m.NMp, m.slots, B, move_table(m), beta_star,
-                                              1.0f / (float)B, m.dZ, m.loss);
+                                              1.0f / (float)B, m.dZ, loss ? loss : m.loss);
+  if (m.use_tc) {
+    // tcgen05: dH = (dZ W^T) * [H > 0] with W streamed as B, on s; the
+    // weight and bias gradients (K-major copies, a fixed-order K split) on a
+    // side stream, each as soon as its activation gradient exists; s waits
+    // for the side stream at the end
+    BwdSpace w;
+    e = bwd_workspace(m, B, &w);
+    if (e == cudaSuccess) e = side_stream(m);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int sms = device_sm_count(dev);
+    e = cudaEventRecord(m.ev[0], s);                               // dZ
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(m.side, m.ev[0], 0);
+    if (e == cudaSuccess)
+      e = weight_grad_tc(m, B, m.H2, kHidden, m.dZ, m.NMp, m.gW3, m.gb3, w, sms, m.side);
+    if (e != cudaSuccess) return e;
+    TcGemmArgs t;
+    std::memset(&t, 0, sizeof(t));
+    t.M = B; t.N = kHidden; t.K = m.NMp; t.err = m.tc_err; t.aux = m.H2; t.ldaux = kHidden;
+    e = gemm_tc_launch<kTcEpiMaskBf16, true>(t, m.tmBA[0], m.tmBB[0], m.tmBC[0], s);
+    if (e == cudaSuccess) e = cudaEventRecord(m.ev[1], s);        // dH2
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(m.side, m.ev[1], 0);
+    if (e == cudaSuccess)
+      e = weight_grad_tc(m, B, m.H1, kHidden, m.dH2, kHidden, m.gW2, m.gb2, w, sms, m.side);
+    if (e != cudaSuccess) return e;
+    t.K = kHidden; t.aux = m.H1;
+    e = gemm_tc_launch<kTcEpiMaskBf16, true>(t, m.tmBA[1], m.tmBB[1], m.tmBC[1], s);
+    if (e == cudaSuccess) e = cudaEventRecord(m.ev[2], s);        // dH1
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(m.side, m.ev[2], 0);
+    if (e == cudaSuccess)
+      e = weight_grad_tc(m, B, m.X, m.K1, m.dH1, kHidden, m.gW1, m.gb1, w, sms, m.side);
+    if (e == cudaSuccess) e = cudaEventRecord(m.ev[3], m.side);   // every gradient
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m.ev[3], 0);
+    return e;
+  }
   GemmArgs g;
   std::memset(&g, 0, sizeof(g));
   const int sp = splits_for(B);
@@ -357,10 +604,9 @@ cudaError_t mlp_backward_dev(Mlp& m, int B, float beta_star, cudaStream_t s) {
   e = gemm<true, false, EPI_ATOMIC>(g, sp, s);
   if (e != cudaSuccess) return e;
   // bias gradients: column sums
-  const int rpb = 512;
-  colsum_kernel<<<dim3((m.NMp + 127) / 128, (B + rpb - 1) / rpb), 128, 0, s>>>(m.dZ, B, m.NMp, rpb, m.gb3);
-  colsum_kernel<<<dim3(kHidden / 128, (B + rpb - 1) / rpb), 128, 0, s>>>(m.dH2, B, kHidden, rpb, m.gb2);
-  colsum_kernel<<<dim3(kHidden / 128, (B + rpb - 1) / rpb), 128, 0, s>>>(m.dH1, B, kHidden, rpb, m.gb1);
+  colsum(m, m.dZ, B, m.NMp, m.gb3, s);
+  colsum(m, m.dH2, B, kHidden, m.gb2, s);
+  colsum(m, m.dH1, B, kHidden, m.gb1, s);
   return cudaGetLastError();
 }
 
@@ -414,6 +660,7 @@ int mlp_create(int variant, int n, int max_batch, uint64_t seed, Mlp** out) {
   const size_t o_dz = off; off = al256(off + B * m->NMp * 2);
   const size_t o_z = off; off = al256(off + B * m->NMp * 4);
   const size_t o_loss = off; off = al256(off + 4);
+  const size_t o_cp = off; off = al256(off + (B / 128) * (size_t)m->NMp * 4);
   const size_t o_wt = off; off = al256(off + (w1 + w2 + w3) * 2);
   const size_t o_err = off; off = al256(off + 4);
   char* p = nullptr;
@@ -441,6 +688,7 @@ int mlp_create(int variant, int n, int max_batch, uint64_t seed, Mlp** out) {
   m->dZ = (__nv_bfloat16*)(p + o_dz);
   m->Z = (float*)(p + o_z);
   m->loss = (float*)(p + o_loss);
+  m->colpart = (float*)(p + o_cp);
   __nv_bfloat16* wt = (__nv_bfloat16*)(p + o_wt);
   m->W1t = wt; m->W2t = wt + w1; m->W3t = wt + w1 + w2;
   m->tc_err = (unsigned*)(p + o_err);
@@ -541,6 +789,13 @@ extern "C" int sk_mlp_create(int variant, int n, int max_batch, uint64_t seed, v
 extern "C" void sk_mlp_destroy(void* model) {
   Mlp* m = (Mlp*)model;
   if (!m) return;
+  if (m->side) {
+    cudaStreamSynchronize(m->side);
+    for (int i = 0; i < 4; ++i)
+      if (m->ev[i]) cudaEventDestroy(m->ev[i]);
+    cudaStreamDestroy(m->side);
+  }
+  if (m->bwd_ws) cudaFree(m->bwd_ws);
   cudaFree(m->block);
   delete m;
 }
@@ -662,12 +917,14 @@ int mlp_train_impl(Mlp& m, const uint8_t* states, uint64_t count, int epochs, in
   unsigned char* dstates = nullptr;
   unsigned* didx = nullptr;
   float* hloss = nullptr;
+  float* dloss = nullptr;                 // per-step losses of an epoch, read back once
   cudaStream_t s = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&dstates, count * m.n);
   if (e == cudaSuccess) e = cudaMalloc(&didx, count * sizeof(unsigned));
   if (e == cudaSuccess) e = cudaHostAlloc(&hloss, steps * sizeof(float), cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaMalloc(&dloss, steps * sizeof(float));
   if (e == cudaSuccess) e = cudaMemcpy(dstates, states, count * m.n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -681,12 +938,13 @@ int mlp_train_impl(Mlp& m, const uint8_t* states, uint64_t count, int epochs, in
     if (seed != SK_MLP_KEEP_ORDER) std::shuffle(perm.begin(), perm.end(), rng);
     e = cudaMemcpyAsync(didx, perm.data(), count * sizeof(unsigned), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // perm is reused next epoch
+    if (e == cudaSuccess) e = cudaMemsetAsync(dloss, 0, steps * sizeof(float), s);
     for (uint64_t st = 0; st < steps && e == cudaSuccess; ++st) {
       const size_t tot = (size_t)batch * m.n;
       gather_slots_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(dstates, didx + st * batch,
                                                                        batch, m.n, m.slots);
       e = mlp_forward_dev(m, batch, s);
-      if (e == cudaSuccess) e = mlp_backward_dev(m, batch, beta_star, s);
+      if (e == cudaSuccess) e = mlp_backward_dev(m, batch, beta_star, s, dloss + st);
       if (e != cudaSuccess) break;
       m.adam_t += 1;
       const float c1 = 1.f - std::pow(0.9f, (float)m.adam_t);
@@ -694,8 +952,10 @@ int mlp_train_impl(Mlp& m, const uint8_t* states, uint64_t count, int epochs, in
       adam_kernel<<<1024, 256, 0, s>>>(m.mW1, m.gW1, m.am, m.av, m.nparams, lr, 0.9f, 0.999f,
                                        1e-8f, c1, c2, m.W1, nwb);
       m.wt_dirty = 1;
-      e = cudaMemcpyAsync(&hloss[st], m.loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+      e = cudaGetLastError();
     }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hloss, dloss, steps * sizeof(float), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) {
       double acc = 0;
@@ -711,6 +971,7 @@ int mlp_train_impl(Mlp& m, const uint8_t* states, uint64_t count, int epochs, in
   if (e1) cudaEventDestroy(e1);
   cudaFree(dstates);
   cudaFree(didx);
+  cudaFree(dloss);
   if (hloss) cudaFreeHost(hloss);
   if (s) cudaStreamDestroy(s);
   if (e != cudaSuccess) return cuda_status(e);

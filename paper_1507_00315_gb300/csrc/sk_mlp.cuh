@@ -41,8 +41,17 @@ struct Mlp {
   // boxes [256][64]); results C = H1, H2 (bf16, boxes [32][64]) and Z (fp32,
   // boxes [32][32])
   CUtensorMap tmA[3], tmB[3], tmC[3];
+  CUtensorMap tmZb;                          // Z's memory as bf16 [max_batch][NMp] (learned chains)
+  // tcgen05 backward: A = dZ, dH2; B = W3, W2 (stored [in][out] = [N][K]);
+  // C = dH2, dH1 (bf16, masked by H2 > 0, H1 > 0)
+  CUtensorMap tmBA[2], tmBB[2], tmBC[2];
+  void* bwd_ws;                              // K-major operand copies + K-split partials
+  size_t bwd_bytes;
+  cudaStream_t side;                         // the backward's weight-gradient stream
+  cudaEvent_t ev[4];                         // its fork and join points
   float* Z;
   float* loss;                               // [1]
+  float* colpart;                            // [max_batch / 128][NMp]: bias-gradient partials
   void* block;                               // one allocation holding all of the above
 };
 
@@ -74,8 +83,9 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // Forward pass for B (multiple of 128) states whose start slots are in
-// m.slots: X, H1, H2 (bf16) and the logits Z (fp32, [B][NMp]).
-cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s);
+// m.slots: X, H1, H2 (bf16) and the logits Z (fp32, [B][NMp]; with
+// logits_bf16, bf16 [B][NMp] in the first half of Z's memory).
+cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s, bool logits_bf16 = false);
 MoveTable move_table(const Mlp& m);
 
 }  // namespace sk

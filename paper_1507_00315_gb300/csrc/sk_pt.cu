@@ -14,33 +14,53 @@
 
 namespace sk {
 
+// Barrier of the two warps of ladder `lw` (0 or 1) of a block of 4 warps:
+// named barriers 1 and 2, 64 threads (constant ids, so the kernel reserves
+// three barriers, not sixteen).
+__device__ __forceinline__ void ladder_pair_sync(int lw) {
+  if (lw == 0)
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+  else
+    asm volatile("bar.sync 2, 64;" ::: "memory");
+}
+
 // Per-warp view of one ladder's tables and this lane's per-rung constants.
+// A ladder has W warps (W = 1: up to 32 rungs; W = 2: up to 64): lane j of
+// warp h serves rung 32 h + j, and the tables have C = 32 W columns.
 struct PtLane {
-  unsigned short* hist;                 // [E][32]
-  unsigned char* slot;                  // [k][32], k = 1..n
-  unsigned char* occ;                   // [b][32]
+  unsigned short* hist;                 // [E][C]
+  unsigned char* slot;                  // [k][C], k = 1..n
+  unsigned char* occ;                   // [b][C]
   unsigned long long tm1, tm2;          // move thresholds at this lane's rung, dE = 1, 2
   const unsigned long long* tswap;      // [M][bins+1]
-  int lane, M, n, delta, bins, nb;
+  int rung, M, n, delta, bins, nb;
   unsigned burnin;
-  bool active;                          // lane < M
+  bool active;                          // rung < M
+  // W = 2: the rung pair (31, 32) across the two warps meets in `xs`
+  // (double-buffered by iteration parity) at named barrier `bar`
+  unsigned* xs;                         // [2][3]: pk of rung 31, its word 3, pk of rung 32
+  int lw;                               // ladder of the block
 };
 
-// Iteration t at rung `lane`, Philox block wc: the energy statistic, one
+// Iteration t at rung S.rung, Philox block wc: the energy statistic, one
 // Metropolis move of the configuration in column c (energy E), then the
-// exchange of this lane's pair (j, j+1), j = t mod 2.  Branch-free: every
+// exchange of this rung's pair (j, j+1), j = t mod 2.  Branch-free: every
 // store and the threshold load happen, with unchanged values where a move
-// or exchange is rejected.
+// or exchange is rejected.  With two warps a ladder, the pair (31, 32) is
+// exchanged through shared memory on odd iterations, after a barrier of the
+// two warps (also the point where the columns that change warp become the
+// other warp's).
+template <int W>
 __device__ __forceinline__ void pt_step(const PtLane& S, const uint4 wc, const unsigned t, int& c,
                                         int& E, unsigned& accm, unsigned& accs) {
-  const int lane = S.lane;
-  const unsigned xw_lo = __shfl_up_sync(0xffffffffu, wc.w, 1);    // word 3 of rung lane-1
-  S.hist[E * 32 + lane] += (unsigned short)(S.active && t >= S.burnin);
+  constexpr int C = 32 * W;
+  unsigned xw_lo = __shfl_up_sync(0xffffffffu, wc.w, 1);          // word 3 of rung - 1
+  S.hist[E * C + S.rung] += (unsigned short)(S.active && t >= S.burnin);
   // Metropolis move: pair k to another start slot
   const int k = 1 + (int)__umulhi(wc.x, (unsigned)S.n);
   const int d = k + S.delta;
   const int L = S.bins - d;
-  unsigned char* sk = &S.slot[k * 32 + c];
+  unsigned char* sk = &S.slot[k * C + c];
   const int s_old = *sk;
   // L = 1 (Langford n = 2, k = 2): no other slot; s_new = s_old keeps the
   // reads inside the table and the move is never taken
@@ -49,10 +69,10 @@ __device__ __forceinline__ void pt_step(const PtLane& S, const uint4 wc, const u
     s_new = (int)__umulhi(wc.y, (unsigned)(L - 1));
     s_new += s_new >= s_old;
   }
-  unsigned char* o1 = &S.occ[s_old * 32 + c];
-  unsigned char* o2 = &S.occ[(s_old + d) * 32 + c];
-  unsigned char* o3 = &S.occ[s_new * 32 + c];
-  unsigned char* o4 = &S.occ[(s_new + d) * 32 + c];
+  unsigned char* o1 = &S.occ[s_old * C + c];
+  unsigned char* o2 = &S.occ[(s_old + d) * C + c];
+  unsigned char* o3 = &S.occ[s_new * C + c];
+  unsigned char* o4 = &S.occ[(s_new + d) * C + c];
   const int a1 = *o1, a2 = *o2, a3 = *o3, a4 = *o4;
   // dE: taking the pair out empties the bins it was alone in; putting it
   // back fills the empty bins it lands on (a new bin may be the old pair's
@@ -76,10 +96,20 @@ __device__ __forceinline__ void pt_step(const PtLane& S, const uint4 wc, const u
   // exchange: both lanes of a pair take the same decision from the lower
   // rung's word 3
   const int pk = (E << 8) | c;
-  const int dn = __shfl_down_sync(0xffffffffu, pk, 1);
-  const int up = __shfl_up_sync(0xffffffffu, pk, 1);
-  const int par = (lane ^ (int)t) & 1;                // 0: lower lane of its pair, 1: upper
-  const int row = lane - par;                         // the pair (row, row + 1)
+  int dn = __shfl_down_sync(0xffffffffu, pk, 1);
+  int up = __shfl_up_sync(0xffffffffu, pk, 1);
+  if constexpr (W == 2) {
+    if (t & 1u) {                                     // the pair (31, 32) is active
+      unsigned* x = S.xs + 3 * (int)((t >> 1) & 1u);
+      if (S.rung == 31) { x[0] = (unsigned)pk; x[1] = wc.w; }
+      if (S.rung == 32) x[2] = (unsigned)pk;
+      ladder_pair_sync(S.lw);
+      if (S.rung == 31) dn = (int)x[2];
+      if (S.rung == 32) { up = (int)x[0]; xw_lo = x[1]; }
+    }
+  }
+  const int par = (S.rung ^ (int)t) & 1;              // 0: lower rung of its pair, 1: upper
+  const int row = S.rung - par;                       // the pair (row, row + 1)
   const bool valid = row >= 0 && row + 1 < S.M;
   const int o = par ? up : dn;
   const int de = par ? (o >> 8) - E : E - (o >> 8);
@@ -91,94 +121,104 @@ __device__ __forceinline__ void pt_step(const PtLane& S, const uint4 wc, const u
   accs += dec && !par;
 }
 
-// One warp = one ladder; persistent over ladders.  Per iteration t, in the
-// order of Algorithm 2: the energy statistics of every rung (after burn-in),
-// one Metropolis move per configuration, then the exchanges of the pairs
-// (j, j+1) with j = t mod 2.  Lane j serves rung j (see sk_pt.cuh): it holds
-// the column c of the configuration now at rung j and its energy E.
+// W warps = one ladder (W = 1: up to 32 rungs, W = 2: up to 64); persistent
+// over ladders.  Per iteration t, in the order of Algorithm 2: the energy
+// statistics of every rung (after burn-in), one Metropolis move per
+// configuration, then the exchanges of the pairs (j, j+1) with j = t mod 2.
+// Lane j of warp h serves rung 32 h + j (see sk_pt.cuh): it holds the column
+// c of the configuration now at that rung and its energy E.
+template <int W>
 __global__ void __launch_bounds__(128, 7)
     pt_kernel(PtParams p, const unsigned long long* __restrict__ tmove_g,
               const unsigned long long* __restrict__ tswap_g, unsigned long long* hist_g,
               unsigned long long* accm_g, unsigned long long* accs_g, unsigned char* final_slots) {
+  constexpr int C = 32 * W;
   extern __shared__ __align__(16) unsigned char pt_smem[];
+  __shared__ unsigned xslot[2][6];                    // W = 2: per ladder of the block
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lw = warp / W, h = warp % W;              // ladder of the block, warp in the ladder
+  const int rung = 32 * h + lane;
   const int M = p.M, n = p.n, bins = p.bins, nb = bins + 1;
-  unsigned char* wbase = pt_smem + (size_t)warp * pt_warp_bytes(n);
+  unsigned char* wbase = pt_smem + (size_t)lw * pt_ladder_bytes(n, W);
   PtLane S;
   S.hist = (unsigned short*)wbase;
-  S.slot = wbase + ((size_t)nb * 64 + 15) / 16 * 16;
-  S.occ = S.slot + (n + 1) * 32;
-  S.lane = lane;
+  S.slot = wbase + pt_hist_bytes(n, W);
+  S.occ = S.slot + (n + 1) * C;
+  S.rung = rung;
   S.M = M;
   S.n = n;
   S.delta = p.delta;
   S.bins = bins;
   S.nb = nb;
   S.burnin = p.burnin;
-  S.active = lane < M;
-  S.tm1 = S.active ? __ldg(&tmove_g[lane * 2]) : 0ull;
-  S.tm2 = S.active ? __ldg(&tmove_g[lane * 2 + 1]) : 0ull;
+  S.active = rung < M;
+  S.tm1 = S.active ? __ldg(&tmove_g[rung * 2]) : 0ull;
+  S.tm2 = S.active ? __ldg(&tmove_g[rung * 2 + 1]) : 0ull;
   S.tswap = tswap_g;
+  S.xs = xslot[lw & 1];
+  S.lw = lw;
   unsigned short* hist = S.hist;
   unsigned char* slot = S.slot;
   unsigned char* occ = S.occ;
   const bool active = S.active;
-  for (int ladder = blockIdx.x * p.warps_per_block + warp; ladder < p.ladders;
-       ladder += gridDim.x * p.warps_per_block) {
-    for (int e = 0; e < nb; ++e) hist[e * 32 + lane] = 0;
-    for (int b = 0; b < bins; ++b) occ[b * 32 + lane] = 0;
-    for (int k = 0; k <= n; ++k) slot[k * 32 + lane] = 0;
-    // column `lane` <- the configuration that starts at rung `lane`
-    int c = lane, E = 0;
+  const int lpb = p.warps_per_block / W;              // ladders per block
+  for (int ladder = blockIdx.x * lpb + lw; ladder < p.ladders; ladder += gridDim.x * lpb) {
+    for (int e = 0; e < nb; ++e) hist[e * C + rung] = 0;
+    for (int b = 0; b < bins; ++b) occ[b * C + rung] = 0;
+    for (int k = 0; k <= n; ++k) slot[k * C + rung] = 0;
+    // column `rung` <- the configuration that starts at that rung
+    int c = rung, E = 0;
     unsigned accm = 0, accs = 0;
     if (active) {
       for (int k = 1; k <= n; ++k) {
         const unsigned L = (unsigned)(bins - (k + p.delta));
         const uint4 w = philox4x32_10_rk(
-            make_uint4((unsigned)k, (unsigned)lane, (unsigned)ladder, 1u), p.rk);
+            make_uint4((unsigned)k, (unsigned)rung, (unsigned)ladder, 1u), p.rk);
         const int s = (int)__umulhi(w.x, L);
-        slot[k * 32 + lane] = (unsigned char)s;
-        occ[s * 32 + lane] += 1;
-        occ[(s + k + p.delta) * 32 + lane] += 1;
+        slot[k * C + rung] = (unsigned char)s;
+        occ[s * C + rung] += 1;
+        occ[(s + k + p.delta) * C + rung] += 1;
       }
-      for (int b = 0; b < bins; ++b) E += occ[b * 32 + lane] == 0;
+      for (int b = 0; b < bins; ++b) E += occ[b * C + rung] == 0;
     }
     __syncwarp();
     for (unsigned long long t0 = 0; t0 < p.iters; t0 += kPtFlush) {
       const unsigned t1 = (unsigned)(t0 + kPtFlush < p.iters ? t0 + kPtFlush : p.iters);
       // two iterations a trip, each one's Philox block computed while the
       // other waits on shared memory (the blocks do not depend on the state)
-      uint4 wa = philox4x32_10_rk(make_uint4((unsigned)t0, (unsigned)lane, (unsigned)ladder, 2u), p.rk);
+      uint4 wa = philox4x32_10_rk(make_uint4((unsigned)t0, (unsigned)rung, (unsigned)ladder, 2u), p.rk);
       unsigned t = (unsigned)t0;
       for (; t + 1 < t1; t += 2) {
-        const uint4 wb = philox4x32_10_rk(make_uint4(t + 1u, (unsigned)lane, (unsigned)ladder, 2u), p.rk);
-        pt_step(S, wa, t, c, E, accm, accs);
-        wa = philox4x32_10_rk(make_uint4(t + 2u, (unsigned)lane, (unsigned)ladder, 2u), p.rk);
-        pt_step(S, wb, t + 1, c, E, accm, accs);
+        const uint4 wb = philox4x32_10_rk(make_uint4(t + 1u, (unsigned)rung, (unsigned)ladder, 2u), p.rk);
+        pt_step<W>(S, wa, t, c, E, accm, accs);
+        wa = philox4x32_10_rk(make_uint4(t + 2u, (unsigned)rung, (unsigned)ladder, 2u), p.rk);
+        pt_step<W>(S, wb, t + 1, c, E, accm, accs);
       }
-      if (t < t1) pt_step(S, wa, t, c, E, accm, accs);
+      if (t < t1) pt_step<W>(S, wa, t, c, E, accm, accs);
       if (t1 < p.iters && active) {                // 16-bit counters: flush this rung's column
         unsigned long long* hist_l =
             hist_g + (size_t)pt_group(ladder, p.ladders, p.groups) * M * nb;
         for (int e = 0; e < nb; ++e) {
-          const unsigned v = hist[e * 32 + lane];
-          if (v) { atomicAdd(&hist_l[(size_t)lane * nb + e], (unsigned long long)v); hist[e * 32 + lane] = 0; }
+          const unsigned v = hist[e * C + rung];
+          if (v) { atomicAdd(&hist_l[(size_t)rung * nb + e], (unsigned long long)v); hist[e * C + rung] = 0; }
         }
       }
     }
+    if constexpr (W == 2) ladder_pair_sync(lw);
     // flush this ladder
     if (active) {
       unsigned long long* hist_l = hist_g + (size_t)pt_group(ladder, p.ladders, p.groups) * M * nb;
       for (int e = 0; e < nb; ++e) {
-        const unsigned v = hist[e * 32 + lane];
-        if (v) atomicAdd(&hist_l[(size_t)lane * nb + e], (unsigned long long)v);
+        const unsigned v = hist[e * C + rung];
+        if (v) atomicAdd(&hist_l[(size_t)rung * nb + e], (unsigned long long)v);
       }
-      if (accm) atomicAdd(&accm_g[lane], (unsigned long long)accm);
-      if (accs) atomicAdd(&accs_g[lane], (unsigned long long)accs);
+      if (accm) atomicAdd(&accm_g[rung], (unsigned long long)accm);
+      if (accs) atomicAdd(&accs_g[rung], (unsigned long long)accs);
       if (final_slots)
         for (int k = 1; k <= n; ++k)
-          final_slots[((size_t)ladder * M + lane) * n + (k - 1)] = slot[k * 32 + c];
+          final_slots[((size_t)ladder * M + rung) * n + (k - 1)] = slot[k * C + c];
     }
+    if constexpr (W == 2) ladder_pair_sync(lw);
     __syncwarp();
   }
 }
@@ -242,6 +282,7 @@ int pt_run_impl(int variant, int n, int M, const double* beta, int L, uint64_t i
   p.M = M;
   p.bins = bins;
   p.ladders = L;
+  const int W = M > 32 ? 2 : 1;                  // warps a ladder
   p.warps_per_block = 4;
   p.iters = (unsigned)iters;
   p.burnin = (unsigned)std::min<uint64_t>(burnin, iters);
@@ -276,22 +317,24 @@ int pt_run_impl(int variant, int n, int M, const double* beta, int L, uint64_t i
   e = cudaMemcpyAsync(dtm, tm.data(), tm.size() * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dts, ts.data(), ts.size() * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(dh, 0, (n_hist + 2 * (size_t)M) * 8, s);
-  const size_t smem = pt_smem_bytes(n, p.warps_per_block);
+  const size_t smem = pt_smem_bytes(n, W, p.warps_per_block);
+  const auto kernel = W == 2 ? pt_kernel<2> : pt_kernel<1>;
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(pt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pt_kernel, 32 * p.warps_per_block, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * p.warps_per_block, smem);
   int grid = sms * (per_sm > 0 ? per_sm : 1);
-  const int need = (L + p.warps_per_block - 1) / p.warps_per_block;
+  const int lpb = p.warps_per_block / W;
+  const int need = (L + lpb - 1) / lpb;
   if (grid > need) grid = need;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e == cudaSuccess) e = cudaEventRecord(e0, s);
   if (e == cudaSuccess) {
-    pt_kernel<<<grid, 32 * p.warps_per_block, smem, s>>>(p, dtm, dts, dh, dam, das, dfin);
+    kernel<<<grid, 32 * p.warps_per_block, smem, s>>>(p, dtm, dts, dh, dam, das, dfin);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaEventRecord(e1, s);
@@ -458,6 +501,7 @@ int pt_estimate_impl(int variant, int n, uint64_t budget, const sk_pt_opts* o, d
   const int proposal = o ? o->proposal : SK_PT_PLAIN;
   if (M < 1 || M > kPtMaxRungs || L < 1 || burnin >= budget) return SK_EINVAL;
   if (proposal != SK_PT_PLAIN && proposal != SK_PT_LEARNED) return SK_EINVAL;
+  if (proposal == SK_PT_LEARNED && M > kPtMaxRungsLearned) return SK_EINVAL;
   if (variant != SK_SKOLEM && variant != SK_LANGFORD) return SK_EINVAL;
   if (n < 2 || n > kPtMaxN) return SK_EINVAL;
   std::vector<double> beta(M);

@@ -3,13 +3,16 @@
 //
 // State space: the simplified problem of Sec. 3 -- pair k sits at any start
 // bin s in [0, 2n - d_k) of 2n bins, overlaps allowed; the energy is the
-// number of empty bins.  One warp runs one ladder of M <= 32 temperatures.
-// Lane j always serves rung j; the configurations stay where they started
-// (column l of the warp's start-slot and bin-occupancy tables in shared
+// number of empty bins.  W warps run one ladder of M <= 32 W temperatures
+// (W = 1 up to 32 rungs, W = 2 up to 64).  Lane j of the ladder's warp h
+// always serves rung 32 h + j; the configurations stay where they started
+// (column l of the ladder's start-slot and bin-occupancy tables in shared
 // memory belongs to the configuration that started at rung l) and an
-// exchange of rungs j, j+1 swaps the column indices and energies that lanes
-// j and j+1 hold.  Per-rung quantities (thresholds, acceptance counters,
-// the energy histogram column) therefore stay with one lane.
+// exchange of rungs j, j+1 swaps the column indices and energies that their
+// lanes hold (a warp shuffle; between rungs 31 and 32, a shared-memory slot
+// and a barrier of the two warps).  Per-rung quantities (thresholds,
+// acceptance counters, the energy histogram column) therefore stay with one
+// lane.
 //
 // Random numbers: Philox-4x32-10 (Salmon et al., SC'11), one call per
 // (counter, key): counter (k, rung, ladder, 1) for the start slot of pair k,
@@ -26,7 +29,8 @@
 
 namespace sk {
 
-constexpr int kPtMaxRungs = 32;
+constexpr int kPtMaxRungs = 64;        // plain chains: two warps a ladder above 32
+constexpr int kPtMaxRungsLearned = 32; // the learned chains' exchange kernel: one warp a ladder
 constexpr int kPtMaxN = 64;      // plain chains (the paper's closing estimate is S(64))
 constexpr int kMlpMaxN = 40;     // the learned proposal (its move table, input width 128)
 constexpr int kPtErrorGroups = 16;   // ladder groups behind pt_estimate's standard error
@@ -34,7 +38,7 @@ constexpr int kPtErrorGroups = 16;   // ladder groups behind pt_estimate's stand
 struct PtParams {
   int n, delta, M, bins;          // bins = 2n
   int ladders;                    // L
-  int warps_per_block;
+  int warps_per_block;            // a multiple of the warps per ladder
   unsigned iters, burnin;
   unsigned key0, key1;
   unsigned rk[20];                // Philox round keys: (key0 + r W0, key1 + r W1), r = 0..9
@@ -71,19 +75,21 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const unsigned* rk) {
   return c;
 }
 
-// Shared-memory layout of one warp: the energy histogram ([E][rung] 16-bit
-// counters, flushed to global memory every kPtFlush iterations), then the
-// start slots ([k][column]) and bin occupancies ([b][column]), one byte an
-// entry.  Thresholds stay in registers (moves) and global memory, L1-cached
-// (exchanges).
+// Shared-memory layout of one ladder of W warps (32 W columns): the energy
+// histogram ([E][rung] 16-bit counters, flushed to global memory every
+// kPtFlush iterations), then the start slots ([k][column]) and bin
+// occupancies ([b][column]), one byte an entry.  Thresholds stay in
+// registers (moves) and global memory, L1-cached (exchanges).
 constexpr unsigned kPtFlush = 32768;
-__host__ __device__ inline size_t pt_warp_bytes(int n) {
-  const size_t hist = ((size_t)(2 * n + 1) * 32 * 2 + 15) / 16 * 16;
-  const size_t st = (size_t)(n + 1) * 32 + (size_t)(2 * n) * 32;
-  return (hist + st + 15) / 16 * 16;
+__host__ __device__ inline size_t pt_hist_bytes(int n, int W) {
+  return ((size_t)(2 * n + 1) * 32 * W * 2 + 15) / 16 * 16;
 }
-__host__ __device__ inline size_t pt_smem_bytes(int n, int wpb) {
-  return (size_t)wpb * pt_warp_bytes(n);
+__host__ __device__ inline size_t pt_ladder_bytes(int n, int W) {
+  const size_t st = (size_t)(n + 1) * 32 * W + (size_t)(2 * n) * 32 * W;
+  return (pt_hist_bytes(n, W) + st + 15) / 16 * 16;
+}
+__host__ __device__ inline size_t pt_smem_bytes(int n, int W, int wpb) {
+  return (size_t)(wpb / W) * pt_ladder_bytes(n, W);
 }
 
 // Host helpers shared by the plain and the learned chains (sk_pt.cu).

@@ -28,7 +28,7 @@ struct LearnedDev {
   int* E;                    // [B]
   int* rung;                 // [B]
   int* lor;                  // [L][M]: configuration holding rung j
-  float* Zcur;               // [B][NMp] logits of the current states
+  __nv_bfloat16* Zcur;       // [B][NMp] logits of the current states (bf16)
   float* lse;                // [B] log-normaliser over their valid moves
   int4* prop;                // [B] (k, old slot, new slot, dE)
   float* lq_fwd;             // [B] log q(C' | C)
@@ -41,16 +41,21 @@ struct LearnedDev {
 
 // Per-block tables of the move layout: the pair k and the start slot of
 // every move m (moves of pair k are off[k] .. off[k+1]-1), so a lane tests
-// "m is a valid move" (its slot is not the pair's current one) with two
-// shared-memory loads.
-constexpr int kMaxMoves = 2560;        // sum_k (2n - d_k) for n <= kMlpMaxN
+// "m is a valid move" (its slot is not the pair's current one) from the
+// tables and the state's slots in shared memory.
+constexpr int kMaxMoves = 2560;        // sum_k (2n - d_k) for n <= kMlpMaxN, padded to 256
 struct MoveMaps {
-  unsigned char k[kMaxMoves];
-  unsigned char s[kMaxMoves];
+  __align__(16) unsigned char k[kMaxMoves];
+  __align__(16) unsigned char s[kMaxMoves];
 };
 
 __device__ __forceinline__ void build_move_maps(const MoveTable& mt, MoveMaps& mm) {
-  for (int m = threadIdx.x; m < mt.NM; m += blockDim.x) {
+  for (int m = threadIdx.x; m < kMaxMoves; m += blockDim.x) {
+    if (m >= mt.NM) {                      // padding: pair 0, never valid (slot 0 of pair 0 = 0)
+      mm.k[m] = 0;
+      mm.s[m] = 0;
+      continue;
+    }
     int lo = 1, hi = mt.n;                 // the pair with off[k] <= m < off[k+1]
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -63,11 +68,13 @@ __device__ __forceinline__ void build_move_maps(const MoveTable& mt, MoveMaps& m
 }
 
 // One warp loads a configuration: lane k-1 takes pair k (slot, and its two
-// bins into the occupancy counts when occ is given).
+// bins into the occupancy counts when occ is given).  s_slot[0] = 0 makes
+// the padding moves (pair 0, slot 0) invalid.
 __device__ __forceinline__ void load_state(const unsigned char* sl, int n, int delta,
                                            unsigned char* s_slot, int* occ, int lane) {
   if (occ)
     for (int i = lane; i < 2 * n; i += 32) occ[i] = 0;
+  if (lane == 0) s_slot[0] = 0;
   __syncwarp();
   for (int k = 1 + lane; k <= n; k += 32) {
     const int s = sl[k - 1];
@@ -80,11 +87,6 @@ __device__ __forceinline__ void load_state(const unsigned char* sl, int n, int d
   __syncwarp();
 }
 
-__device__ __forceinline__ bool valid_move(const MoveMaps& mm, const unsigned char* s_slot,
-                                           int m) {
-  return mm.s[m] != s_slot[mm.k[m]];
-}
-
 // Pull `bytes` bytes at p into L2 (one 128-byte line a lane at a time): a
 // warp asks for the next chain's rows before it works on the current one,
 // so the per-chain loads wait on L2 rather than on HBM.
@@ -94,18 +96,78 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes, int lan
     asm volatile("prefetch.global.L2 [%0];" ::"l"(c + o));
 }
 
-// log sum exp of the logits z over the valid moves of the state in s_slot:
-// a coalesced pass for the maximum, a second (from L1) for the sum.
-__device__ float valid_lse(const float* z, const MoveMaps& mm, int NM,
-                           const unsigned char* s_slot, int lane) {
-  float mx = -INFINITY;
-  for (int m = lane; m < NM; m += 32)
-    if (valid_move(mm, s_slot, m)) mx = fmaxf(mx, z[m]);
-  mx = warp_max(mx);
-  float sum = 0.f;
-  for (int m = lane; m < NM; m += 32)
-    if (valid_move(mm, s_slot, m)) sum += __expf(z[m] - mx);
-  return mx + __logf(warp_sum(sum));
+// A chain's logit row (bf16) held in registers: chunk c of 256 moves, lane l
+// holds moves 256 c + 8 l .. + 7 in one 16-byte word.  Lanes whose 8 moves
+// all lie beyond NM load nothing (their words are never used).
+constexpr int kLtChunks = kMaxMoves / 256;
+struct LogitRow {
+  uint4 w[kLtChunks];
+  unsigned valid[kLtChunks];   // bit i: move 256 c + 8 l + i is a valid move of the state
+};
+
+__device__ __forceinline__ float bf16_lo(unsigned x) { return __uint_as_float(x << 16); }
+__device__ __forceinline__ float bf16_hi(unsigned x) { return __uint_as_float(x & 0xFFFF0000u); }
+__device__ __forceinline__ float row_elem(const uint4& w, int i) {
+  const unsigned x = i < 4 ? (i < 2 ? w.x : w.y) : (i < 6 ? w.z : w.w);
+  return (i & 1) ? bf16_hi(x) : bf16_lo(x);
+}
+
+__device__ __forceinline__ void load_row(const __nv_bfloat16* z, int NM, int lane, LogitRow& r) {
+#pragma unroll
+  for (int c = 0; c < kLtChunks; ++c) {
+    const int m0 = c * 256 + lane * 8;
+    r.w[c] = m0 < NM ? __ldg((const uint4*)(z + m0)) : make_uint4(0, 0, 0, 0);
+  }
+}
+
+// Valid-move bits of the state in s_slot for the row's layout.
+__device__ __forceinline__ void row_valid(const MoveMaps& mm, const unsigned char* s_slot, int NM,
+                                          int lane, LogitRow& r) {
+#pragma unroll
+  for (int c = 0; c < kLtChunks; ++c) {
+    const int m0 = c * 256 + lane * 8;
+    unsigned bits = 0;
+    if (m0 < NM) {
+      const uint2 kk = *(const uint2*)&mm.k[m0];
+      const uint2 ss = *(const uint2*)&mm.s[m0];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const unsigned k = ((i < 4 ? kk.x : kk.y) >> (8 * (i & 3))) & 0xFFu;
+        const unsigned sl = ((i < 4 ? ss.x : ss.y) >> (8 * (i & 3))) & 0xFFu;
+        bits |= (unsigned)(sl != s_slot[k]) << i;
+      }
+    }
+    r.valid[c] = bits;
+  }
+}
+
+// log sum exp of the row over its valid moves, in one pass over the
+// registers: each lane keeps a running maximum and the sum scaled to it
+// (rescaled when the maximum grows), then the lanes' pairs are combined.
+__device__ __forceinline__ float row_lse(const LogitRow& r) {
+  float mx = -INFINITY, sum = 0.f;
+#pragma unroll
+  for (int c = 0; c < kLtChunks; ++c)
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if ((r.valid[c] >> i) & 1u) {
+        const float z = row_elem(r.w[c], i);
+        if (z > mx) {
+          sum = sum * __expf(mx - z) + 1.f;
+          mx = z;
+        } else {
+          sum += __expf(z - mx);
+        }
+      }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const float m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+    const float s2 = __shfl_xor_sync(0xffffffffu, sum, o);
+    const float mn = fmaxf(mx, m2);
+    sum = mn == -INFINITY ? 0.f : sum * __expf(mx - mn) + s2 * __expf(m2 - mn);
+    mx = mn;
+  }
+  return mx + __logf(sum);
 }
 
 __global__ void lt_init_kernel(LearnedDev d) {
@@ -131,7 +193,8 @@ __global__ void lt_init_kernel(LearnedDev d) {
 }
 
 // After a forward pass of the current states: keep their logits and lse.
-__global__ void __launch_bounds__(256, 4) lt_keep_kernel(LearnedDev d, MoveTable mt, const float* Z) {
+__global__ void __launch_bounds__(256, 2) lt_keep_kernel(LearnedDev d, MoveTable mt,
+                                                      const __nv_bfloat16* Z) {
   __shared__ MoveMaps mm;
   __shared__ unsigned char s_slot[8][kPtMaxN + 8];
   build_move_maps(mt, mm);
@@ -139,10 +202,14 @@ __global__ void __launch_bounds__(256, 4) lt_keep_kernel(LearnedDev d, MoveTable
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int c = blockIdx.x * 8 + w; c < d.B; c += gridDim.x * 8) {
     load_state(d.slots + (size_t)c * d.n, d.n, d.delta, s_slot[w], nullptr, lane);
-    const float* z = Z + (size_t)c * d.NMp;
-    float* zc = d.Zcur + (size_t)c * d.NMp;
-    for (int m = lane; m < d.NMp; m += 32) zc[m] = z[m];
-    const float l = valid_lse(z, mm, mt.NM, s_slot[w], lane);
+    LogitRow r;
+    load_row(Z + (size_t)c * d.NMp, mt.NM, lane, r);
+    row_valid(mm, s_slot[w], mt.NM, lane, r);
+    const float l = row_lse(r);
+    __nv_bfloat16* zc = d.Zcur + (size_t)c * d.NMp;
+#pragma unroll
+    for (int k = 0; k < kLtChunks; ++k)
+      if (k * 256 + lane * 8 < mt.NM) *(uint4*)(zc + k * 256 + lane * 8) = r.w[k];
     if (lane == 0) d.lse[c] = l;
     __syncwarp();
   }
@@ -150,10 +217,11 @@ __global__ void __launch_bounds__(256, 4) lt_keep_kernel(LearnedDev d, MoveTable
 
 // Statistics of iteration t, then a move drawn from the current softmax; the
 // proposed configuration goes to `prop_slots` (the network's input).  The
-// draw is an inverse CDF over the valid moves in move order: one coalesced
-// pass for the total, then 32 moves at a time with a warp scan until the
-// running sum passes u * total.
-__global__ void __launch_bounds__(256, 4) lt_propose_kernel(LearnedDev d, MoveTable mt, unsigned t,
+// draw is an inverse CDF over the valid moves in move order, from the row in
+// registers: the chunk sums (warp reductions), the chunk that holds u *
+// total, a scan of its lanes' sums, then the lane that holds it walks its 8
+// moves.
+__global__ void __launch_bounds__(256, 2) lt_propose_kernel(LearnedDev d, MoveTable mt, unsigned t,
                                                          int count_stats,
                                                          unsigned char* prop_slots) {
   __shared__ MoveMaps mm;
@@ -162,46 +230,89 @@ __global__ void __launch_bounds__(256, 4) lt_propose_kernel(LearnedDev d, MoveTa
   build_move_maps(mt, mm);
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int NM = mt.NM;
   for (int c = blockIdx.x * 8 + w; c < d.B; c += gridDim.x * 8) {
     const int cn = c + gridDim.x * 8;
     if (cn < d.B) {
-      prefetch_l2(d.Zcur + (size_t)cn * d.NMp, (size_t)mt.NM * 4, lane);
+      prefetch_l2(d.Zcur + (size_t)cn * d.NMp, (size_t)NM * 2, lane);
       prefetch_l2(d.slots + (size_t)cn * d.n, (size_t)d.n, lane);
     }
-    const int ladder = c / d.M, r = d.rung[c], E = d.E[c];
-    if (lane == 0 && count_stats) d.hist[((size_t)ladder * d.M + r) * d.nb + E] += 1;
+    LogitRow r;
+    load_row(d.Zcur + (size_t)c * d.NMp, NM, lane, r);
+    const int ladder = c / d.M, rg = d.rung[c], E = d.E[c];
+    if (lane == 0 && count_stats) d.hist[((size_t)ladder * d.M + rg) * d.nb + E] += 1;
     load_state(d.slots + (size_t)c * d.n, d.n, d.delta, s_slot[w], s_occ[w], lane);
-    const float* z = d.Zcur + (size_t)c * d.NMp;
+    row_valid(mm, s_slot[w], NM, lane, r);
     const float lse = d.lse[c];
-    const int NM = mt.NM;
-    const uint4 rw = philox4x32_10(make_uint4(t, (unsigned)r, (unsigned)ladder, 5u), d.key0, d.key1);
-    float part = 0.f;
-    for (int m = lane; m < NM; m += 32)
-      if (valid_move(mm, s_slot[w], m)) part += __expf(z[m] - lse);
-    const float total = warp_sum(part);
-    const float target = ((float)rw.x + 0.5f) * 2.3283064365386963e-10f * total;
-    float run = 0.f;
-    int pick = -1, last = -1;
-    for (int base = 0; base < NM; base += 32) {
-      const int m = base + lane;
-      const bool ok = m < NM && valid_move(mm, s_slot[w], m);
-      const float v = ok ? __expf(z[m] - lse) : 0.f;
-      float incl = v;
+    const uint4 rw = philox4x32_10(make_uint4(t, (unsigned)rg, (unsigned)ladder, 5u), d.key0, d.key1);
+    // per lane and chunk: the sum of exp(z - lse) over its valid moves
+    float part[kLtChunks], csum[kLtChunks];
+    float total = 0.f;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const float u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += u;
-      }
-      const unsigned valid = __ballot_sync(0xffffffffu, ok);
-      if (valid) last = base + 31 - __clz(valid);
-      const unsigned hit = __ballot_sync(0xffffffffu, ok && run + incl >= target);
-      if (hit) {
-        pick = base + __ffs(hit) - 1;
-        break;
-      }
-      run += __shfl_sync(0xffffffffu, incl, 31);
+    for (int k = 0; k < kLtChunks; ++k) {
+      float a = 0.f;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if ((r.valid[k] >> i) & 1u) a += __expf(row_elem(r.w[k], i) - lse);
+      part[k] = a;
+      csum[k] = warp_sum(a);
+      total += csum[k];
     }
-    if (pick < 0) pick = last < 0 ? 0 : last;   // rounding left the target just above the total
+    const float target = ((float)rw.x + 0.5f) * 2.3283064365386963e-10f * total;
+    // the chunk: the first whose running sum reaches the target (the last
+    // one with valid moves if rounding leaves the target above the total)
+    float run = 0.f, pk = 0.f;
+    uint4 wk = make_uint4(0, 0, 0, 0);
+    unsigned vk = 0;
+    int kc = -1, klast = 0;
+#pragma unroll
+    for (int k = 0; k < kLtChunks; ++k) {
+      const bool any = __any_sync(0xffffffffu, r.valid[k] != 0u);
+      if (any) klast = k;
+      if (kc < 0 && any && run + csum[k] >= target) {
+        kc = k;
+      } else if (kc < 0) {
+        run += csum[k];
+      }
+    }
+    if (kc < 0) {                          // rounding: take the last chunk with valid moves
+      kc = klast;
+      run = total;                         // every lane of that chunk then falls through to its last move
+#pragma unroll
+      for (int k = 0; k < kLtChunks; ++k)
+        if (k == klast) run -= csum[k];
+    }
+#pragma unroll
+    for (int k = 0; k < kLtChunks; ++k)
+      if (k == kc) { pk = part[k]; wk = r.w[k]; vk = r.valid[k]; }
+    // lanes of the chunk: inclusive scan of their sums
+    float incl = pk;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    const unsigned hit = __ballot_sync(0xffffffffu, vk != 0u && run + incl >= target);
+    const unsigned withv = __ballot_sync(0xffffffffu, vk != 0u);
+    const int ln = hit ? __ffs(hit) - 1 : 31 - __clz(withv);   // withv != 0: the chunk has valid moves
+    int pick_i = -1;
+    if (lane == ln) {
+      float a = run + incl - pk;           // exclusive: the running sum before this lane's moves
+      int last = -1;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if ((vk >> i) & 1u) {
+          last = i;
+          a += __expf(row_elem(wk, i) - lse);
+          if (pick_i < 0 && a >= target) pick_i = i;
+        }
+      }
+      if (pick_i < 0) pick_i = last;
+    }
+    pick_i = __shfl_sync(0xffffffffu, pick_i, ln);
+    const uint4 wp = make_uint4(__shfl_sync(0xffffffffu, wk.x, ln), __shfl_sync(0xffffffffu, wk.y, ln),
+                                __shfl_sync(0xffffffffu, wk.z, ln), __shfl_sync(0xffffffffu, wk.w, ln));
+    const int pick = kc * 256 + ln * 8 + pick_i;
     const int kp = mm.k[pick];
     const int s_new = mm.s[pick], s_old = s_slot[w][kp];
     const int dE = move_delta_e(s_occ[w], s_old, kp + d.delta, s_new);
@@ -210,45 +321,51 @@ __global__ void __launch_bounds__(256, 4) lt_propose_kernel(LearnedDev d, MoveTa
       ps[i] = (i + 1 == kp) ? (unsigned char)s_new : s_slot[w][i + 1];
     if (lane == 0) {
       d.prop[c] = make_int4(kp, s_old, s_new, dE);
-      d.lq_fwd[c] = z[pick] - lse;
+      d.lq_fwd[c] = row_elem(wp, pick_i) - lse;
     }
     __syncwarp();
   }
 }
 
-// Metropolis-Hastings acceptance with the proposed states' logits Zp.
-__global__ void __launch_bounds__(256, 4) lt_accept_kernel(LearnedDev d, MoveTable mt, unsigned t,
+// Metropolis-Hastings acceptance with the proposed states' logits Zp (bf16).
+__global__ void __launch_bounds__(256, 2) lt_accept_kernel(LearnedDev d, MoveTable mt, unsigned t,
                                                         const unsigned char* prop_slots,
-                                                        const float* Zp) {
+                                                        const __nv_bfloat16* Zp) {
   __shared__ MoveMaps mm;
   __shared__ unsigned char s_slot[8][kPtMaxN + 8];
   build_move_maps(mt, mm);
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int NM = mt.NM;
   for (int c = blockIdx.x * 8 + w; c < d.B; c += gridDim.x * 8) {
     const int cn = c + gridDim.x * 8;
     if (cn < d.B) {
-      prefetch_l2(Zp + (size_t)cn * d.NMp, (size_t)mt.NM * 4, lane);
+      prefetch_l2(Zp + (size_t)cn * d.NMp, (size_t)NM * 2, lane);
       prefetch_l2(prop_slots + (size_t)cn * d.n, (size_t)d.n, lane);
     }
-    const int ladder = c / d.M, r = d.rung[c];
+    const __nv_bfloat16* zp = Zp + (size_t)c * d.NMp;
+    LogitRow r;
+    load_row(zp, NM, lane, r);
+    const int ladder = c / d.M, rg = d.rung[c];
     load_state(prop_slots + (size_t)c * d.n, d.n, d.delta, s_slot[w], nullptr, lane);
-    const float* zp = Zp + (size_t)c * d.NMp;
-    const float lse_p = valid_lse(zp, mm, mt.NM, s_slot[w], lane);
+    row_valid(mm, s_slot[w], NM, lane, r);
+    const float lse_p = row_lse(r);
     const int4 pr = d.prop[c];
-    const float lq_rev = zp[mt.off[pr.x] + pr.y] - lse_p;
-    const float log_a = (float)(-d.beta[r] * (double)pr.w) + lq_rev - d.lq_fwd[c];
-    const uint4 rw = philox4x32_10(make_uint4(t, (unsigned)r, (unsigned)ladder, 5u), d.key0, d.key1);
+    const float lq_rev = __bfloat162float(zp[mt.off[pr.x] + pr.y]) - lse_p;
+    const float log_a = (float)(-d.beta[rg] * (double)pr.w) + lq_rev - d.lq_fwd[c];
+    const uint4 rw = philox4x32_10(make_uint4(t, (unsigned)rg, (unsigned)ladder, 5u), d.key0, d.key1);
     const float u = ((float)rw.y + 0.5f) * 2.3283064365386963e-10f;
     const bool acc = log_a >= 0.f || logf(u) < log_a;
     if (acc) {
       for (int i = lane; i < d.n; i += 32) d.slots[(size_t)c * d.n + i] = s_slot[w][i + 1];
-      float* zc = d.Zcur + (size_t)c * d.NMp;
-      for (int m = lane; m < d.NMp; m += 32) zc[m] = zp[m];
+      __nv_bfloat16* zc = d.Zcur + (size_t)c * d.NMp;
+#pragma unroll
+      for (int k = 0; k < kLtChunks; ++k)
+        if (k * 256 + lane * 8 < NM) *(uint4*)(zc + k * 256 + lane * 8) = r.w[k];
       if (lane == 0) {
         d.lse[c] = lse_p;
         d.E[c] += pr.w;
-        d.accm[(size_t)ladder * d.M + r] += 1;
+        d.accm[(size_t)ladder * d.M + rg] += 1;
       }
     }
     __syncwarp();
@@ -300,7 +417,7 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
                    uint64_t* accm, uint64_t* accs, void* stream, double* kernel_ms) {
   Mlp* m = (Mlp*)model;
   if (!m || !beta || !hist || iters > 0xffffffffULL) return SK_EINVAL;
-  if (m->variant != variant || m->n != n || M < 2 || M > kPtMaxRungs || L < 1) return SK_EINVAL;
+  if (m->variant != variant || m->n != n || M < 2 || M > kPtMaxRungsLearned || L < 1) return SK_EINVAL;
   const int B = L * M, Bp = (B + 127) / 128 * 128, nb = 2 * n + 1;
   if (Bp > m->max_batch) return SK_EINVAL;
   int st = check_device();
@@ -331,7 +448,7 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
   const size_t o_E = off; off = al(off + (size_t)B * 4);
   const size_t o_r = off; off = al(off + (size_t)B * 4);
   const size_t o_lor = off; off = al(off + (size_t)B * 4);
-  const size_t o_z = off; off = al(off + (size_t)B * m->NMp * 4);
+  const size_t o_z = off; off = al(off + (size_t)B * m->NMp * 2);
   const size_t o_lse = off; off = al(off + (size_t)B * 4);
   const size_t o_pr = off; off = al(off + (size_t)B * 16);
   const size_t o_lq = off; off = al(off + (size_t)B * 4);
@@ -351,7 +468,7 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
   d.E = (int*)(p + o_E);
   d.rung = (int*)(p + o_r);
   d.lor = (int*)(p + o_lor);
-  d.Zcur = (float*)(p + o_z);
+  d.Zcur = (__nv_bfloat16*)(p + o_z);
   d.lse = (float*)(p + o_lse);
   d.prop = (int4*)(p + o_pr);
   d.lq_fwd = (float*)(p + o_lq);
@@ -374,17 +491,18 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
     lt_init_kernel<<<(B + 255) / 256, 256, 0, s>>>(d);
     e = cudaMemcpyAsync(m->slots, d.slots, (size_t)B * n, cudaMemcpyDeviceToDevice, s);
   }
-  if (e == cudaSuccess) e = mlp_forward_dev(*m, Bp, s);
+  const __nv_bfloat16* Zb = (const __nv_bfloat16*)m->Z;      // the forward's bf16 logits
+  if (e == cudaSuccess) e = mlp_forward_dev(*m, Bp, s, true);
   if (e == cudaSuccess) {
-    lt_keep_kernel<<<chain_grid, 256, 0, s>>>(d, mt, m->Z);
+    lt_keep_kernel<<<chain_grid, 256, 0, s>>>(d, mt, Zb);
     e = cudaGetLastError();
   }
   for (uint64_t t = 0; t < iters && e == cudaSuccess; ++t) {
     lt_propose_kernel<<<chain_grid, 256, 0, s>>>(d, mt, (unsigned)t, t >= burnin ? 1 : 0,
                                                   m->slots);
-    e = mlp_forward_dev(*m, Bp, s);
+    e = mlp_forward_dev(*m, Bp, s, true);
     if (e != cudaSuccess) break;
-    lt_accept_kernel<<<chain_grid, 256, 0, s>>>(d, mt, (unsigned)t, m->slots, m->Z);
+    lt_accept_kernel<<<chain_grid, 256, 0, s>>>(d, mt, (unsigned)t, m->slots, Zb);
     lt_exchange_kernel<<<(L + 3) / 4, 128, 0, s>>>(d, (unsigned)t);
     e = cudaGetLastError();
   }

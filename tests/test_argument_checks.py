@@ -35,7 +35,7 @@ def test_count_options(variant, n, kw):
     (2, 8, [0.0, 1.0], 4, 10, 0, 1),                # hooked: no tempering variant
     (0, 1, [0.0, 1.0], 4, 10, 0, 1),                # n < 2
     (0, 65, [0.0, 1.0], 4, 10, 0, 1),               # above the largest order
-    (0, 8, [float(j) for j in range(33)], 4, 10, 0, 1),   # 33 rungs
+    (0, 8, [float(j) for j in range(65)], 4, 10, 0, 1),   # 65 rungs
     (0, 8, [0.0, 1.0], 0, 10, 0, 1),                # no ladder
     (0, 8, [1.0, 0.5], 4, 10, 0, 1),                # decreasing ladder
     (0, 8, [-1.0, 0.5], 4, 10, 0, 1),               # negative beta
@@ -52,7 +52,8 @@ def test_pt_run_arguments(args):
 @pytest.mark.parametrize("variant,n,budget,kw", [
     (0, 8, 0, {}),                                  # no iterations
     (0, 8, 1 << 32, {}),
-    (0, 8, 1000, {"rungs": 33}),
+    (0, 8, 1000, {"rungs": 65}),
+    (0, 8, 1000, {"rungs": 33, "proposal": sk.PT_LEARNED}),   # learned: one warp a ladder
     (0, 8, 1000, {"burnin_frac": 1.0}),             # burn-in would take every iteration
     (2, 8, 1000, {}),
     (0, 65, 1000, {}),
@@ -96,3 +97,19 @@ def test_learned_proposal_orders():
     with pytest.raises(sk.SkolemError) as e:
         sk.Mlp(0, 41, 128)
     assert e.value.status == sk.SK_EINVAL
+
+
+def test_extended_refusals_before_device_work():
+    # a hole outside 1..2n+1 (0 must not read as "no hole"), a symmetry
+    # option, a walk reaching the hole, a lower hole for the item residues
+    for args, kw in (((12, 0), {}), ((12, -1), {}), ((12, 26), {}), ((0, 1), {}),
+                     ((12, 13), {"symmetry": sk.SYMMETRY_NEGATION_EVEN}),
+                     ((12, 13), {"symmetry": sk.SYMMETRY_REVERSAL}),
+                     ((12, 13), {"walk_bits": 13}), ((3, 4), {})):
+        with pytest.raises(sk.SkolemError) as e:
+            sk.count_extended(*args, **kw)
+        assert e.value.status == sk.SK_EINVAL, (args, kw)
+    for hole in (0, 8, 26):
+        with pytest.raises(sk.SkolemError) as e:
+            sk.extended_item_residues(12, hole, 9, 0, 1, sk.default_primes()[:3])
+        assert e.value.status == sk.SK_EINVAL

@@ -76,3 +76,18 @@ def test_reversal_plan(variant, n):
     assert r["items"] == 2 * per_side
     assert r["terms"] == r["items"] << m
     assert r["items"] * 2 ** m <= 2 ** (2 * n - 1) * (0.5 + 2.0 ** -(depth + 1)) + 1
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("n", [6, 7, 8, 9, 12, 16, 20, 24, 27, 28, 29, 31])
+def test_reversal_with_lemma_2_4_plan(variant, n):
+    # the x_1 = +1 half of the mirrored items in the existence classes
+    # (Skolem n = 0, 1, Langford n = 0, 3 mod 4), nothing outside them
+    r = sk.count_plan(variant, n, symmetry=sk.SYMMETRY_REVERSAL_EVEN)
+    r2 = sk.count_plan(variant, n, symmetry=sk.SYMMETRY_REVERSAL)
+    exists = n % 4 in ((0, 1), (0, 3))[variant]
+    assert r["symmetry"] == sk.SYMMETRY_REVERSAL_EVEN
+    if exists:
+        assert r["walk_bits"] == r2["walk_bits"] and 2 * r["items"] == r2["items"]
+    else:
+        assert r["terms"] == 0 and r["items"] == 0 and r["complete"] == 1

@@ -44,6 +44,29 @@ def test_full_size_against_the_tables(variant, n, skolem_table, langford_table):
     assert rep["symmetry"] == REV
 
 
+@pytest.mark.parametrize("variant", [SK, LA])
+def test_reversal_and_lemma_2_4_together(variant, skolem_table, langford_table):
+    # Lemmas 2.2, 2.3 and 2.4: zero outside the existence classes, else the
+    # x_1 = +1 mirrored items doubled -- the same residues as the plain
+    # half-sum, about a quarter of its terms
+    both = sk.SYMMETRY_REVERSAL_EVEN
+    for n in range(1, 18):
+        c0, r0 = sk.count_ex(variant, n, nprimes=4, convention=sk.COUNT_ALL)
+        c1, r1 = sk.count_ex(variant, n, nprimes=4, convention=sk.COUNT_ALL, symmetry=both)
+        assert c1 == c0 and r1["residues"] == r0["residues"], n
+        if n >= 6:
+            assert r1["symmetry"] == both
+            if c0:
+                pairs = n - 1 - r1["walk_bits"] // 2
+                frac = (0.5 + 2.0 ** -(min(8, pairs) + 1)) / 2
+                assert r1["terms"] <= frac * r0["terms"] + 1, (n, r1["terms"], r0["terms"])
+            else:
+                assert r1["terms"] == 0
+    n = 20
+    c, rep = sk.count_ex(variant, n, symmetry=both)
+    assert c == (skolem_table if variant == SK else langford_table).get(n, 0)
+
+
 def test_walk_widths_and_schedules():
     base = sk.count_ex(LA, 14, nprimes=3)[1]["residues"]
     U = sk.count_plan(LA, 14)["inner_bits"]

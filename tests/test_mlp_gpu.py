@@ -50,16 +50,23 @@ def test_forward_matches_fp64(variant, n, tensor_memory):
     assert err < 2e-2, err
 
 
-@pytest.mark.parametrize("variant,n", [(0, 8), (1, 16)])
-def test_gradients_match_fp64(variant, n):
+@pytest.mark.parametrize("tensor_memory", [True, False])
+@pytest.mark.parametrize("variant,n,B", [(0, 8, 256), (1, 16, 256), (0, 20, 1024)])
+def test_gradients_match_fp64(variant, n, B, tensor_memory):
+    # both backward paths: tcgen05 (activation gradients with B streamed,
+    # weight gradients from K-major copies with a fixed-order K split) and
+    # mma.sync (split-K atomics); B = 1024 gives the tcgen05 weight gradients
+    # a K split over 16 slices
     d = si.differences(variant, n)
     off, nslot = mlp_ref.move_table(n, d)
     nm = int(nslot.sum())
-    model = sk.Mlp(variant, n, 256, seed=2)
+    model = sk.Mlp(variant, n, B, seed=2)
+    model.set_gemm(tensor_memory)
     params = [si.bf16_round(p) for p in si.mlp_params(11, 2 * n, 256, nm)]
     model.set_params(_flat(params))
-    slots = si.random_slots(13, 256, n, d)
+    slots = si.random_slots(13, B, n, d)
     loss, g = model.loss_grad(slots, beta_star=2.0)
+    model.check()
     x = mlp_ref.occupancy(slots, n, d)
     mask = mlp_ref.valid_mask(slots, n, d)
     target = mlp_ref.target_distribution(slots, n, d, 2.0)
@@ -123,9 +130,10 @@ def test_tensor_memory_and_mma_sync_paths_agree(variant, n, batch):
 @pytest.mark.parametrize("variant,n", [(0, 8), (1, 12)])
 def test_training_steps_match_adam_in_fp64(variant, n):
     # Two sk_mlp_train steps on one fixed minibatch of 256 states (given
-    # order, so each step sees exactly the batch sk_mlp_loss_grad sees; at 256
-    # rows the backward has no split-K and one column-sum block, so the GPU's
-    # gradient is the same bits in both calls).  After each step the FP32
+    # order, so each step sees exactly the batch sk_mlp_loss_grad sees; the
+    # tcgen05 backward sums its K-split partials in a fixed order and 256 rows
+    # take one column-sum block, so the GPU's gradient is the same bits in
+    # both calls).  After each step the FP32
     # masters and both moments must equal mlp_ref.adam_step applied in FP64
     # to the pre-step state and that gradient, and the BF16 weight copies the
     # forward uses must be the masters rounded to nearest-even bf16 exactly.

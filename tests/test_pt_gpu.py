@@ -26,6 +26,10 @@ TABLE6_BETA = [float(r[1]) for r in read_golden("table6_pt_s12.txt")]
     (0, 33, 32, 1, 300, 30, 3),            # largest order of the workloads
     (1, 64, 32, 2, 200, 20, 6),            # the largest order (the paper's closing S(64))
     (1, 2, 3, 2, 500, 0, 8),               # Langford n = 2: pair 2 has one slot
+    (0, 5, 33, 3, 1001, 100, 21),          # 33 rungs: two warps a ladder, odd iterations
+    (1, 9, 48, 5, 2000, 200, 22),          # 48 rungs; more ladders than a block holds
+    (0, 6, 64, 2, 70001, 35000, 23),       # 64 rungs; histogram flushes mid-run
+    (0, 64, 64, 1, 300, 30, 24),           # 64 rungs at the largest order
     (0, 6, 7, 3, 70000, 35000, 4),         # odd ladder; histogram flushes mid-run
 ])
 def test_trajectory_equals_oracle(variant, n, M, L, iters, burnin, seed):
@@ -38,13 +42,16 @@ def test_trajectory_equals_oracle(variant, n, M, L, iters, burnin, seed):
     assert np.array_equal(got["final_slots"], want["final_slots"])
 
 
-@pytest.mark.parametrize("variant,n,iters", [(0, 16, 200), (1, 24, 150), (0, 64, 40)])
-def test_trajectory_equals_oracle_at_full_size(variant, n, iters):
+@pytest.mark.parametrize("variant,n,iters,M", [(0, 16, 200, 32), (1, 24, 150, 32),
+                                               (0, 64, 40, 32), (0, 64, 21, 64),
+                                               (1, 40, 41, 48)])
+def test_trajectory_equals_oracle_at_full_size(variant, n, iters, M):
     # the tempering workload's launch: 32 rungs x 4096 ladders, every ladder
     # resident at once (at n = 64 a ladder's tables need more shared memory:
     # fewer are resident and the persistent warps take several ladders each);
-    # a short run so the oracle finishes in seconds
-    beta = list(np.linspace(0.0, 32.0, 32))
+    # 48 and 64 rungs: two warps a ladder; a short run so the oracle finishes
+    # in seconds
+    beta = list(np.linspace(0.0, 32.0, M))
     got = sk.pt_run(variant, n, beta, 4096, iters, iters // 10, 99, want_final=True)
     want = oracle.pt_run(variant, n, beta, 4096, iters, iters // 10, 99, want_final=True)
     assert np.array_equal(got["hist"], want["hist"])
