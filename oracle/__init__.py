@@ -68,6 +68,7 @@ def _load():
                                        ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
                                        ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]
+            lib.orc_pt_run_trips.argtypes = lib.orc_pt_run.argtypes + [ctypes.c_void_p]
             lib.orc_simplified_energy_hist.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
             _lib = lib
     return _lib
@@ -212,9 +213,9 @@ def philox4x32_10(counter, key):
 
 
 def pt_run(variant: int, n: int, beta, ladders: int, iters: int, burnin: int, seed: int,
-           want_final: bool = False):
+           want_final: bool = False, want_trips: bool = False):
     """O3: Algorithm 2.  Returns dict(hist[M, 2n+1], acc_move[M], acc_swap[M],
-    final_slots[L, M, n] or None)."""
+    final_slots[L, M, n] or None, round_trips or None)."""
     lib = _load()
     beta = np.ascontiguousarray(beta, dtype=np.float64)
     M = beta.shape[0]
@@ -222,11 +223,14 @@ def pt_run(variant: int, n: int, beta, ladders: int, iters: int, burnin: int, se
     am = np.zeros(M, dtype=np.uint64)
     asw = np.zeros(M, dtype=np.uint64)
     fin = np.zeros((ladders, M, n), dtype=np.uint8) if want_final else None
-    rc = lib.orc_pt_run(variant, n, M, beta.ctypes.data, ladders, iters, burnin, seed,
-                        hist.ctypes.data, am.ctypes.data, asw.ctypes.data,
-                        fin.ctypes.data if fin is not None else None)
+    trips = np.zeros(1, dtype=np.uint64)
+    rc = lib.orc_pt_run_trips(variant, n, M, beta.ctypes.data, ladders, iters, burnin, seed,
+                              hist.ctypes.data, am.ctypes.data, asw.ctypes.data,
+                              fin.ctypes.data if fin is not None else None,
+                              trips.ctypes.data if want_trips else None)
     _check(rc, "pt_run")
-    return {"hist": hist, "acc_move": am, "acc_swap": asw, "final_slots": fin}
+    return {"hist": hist, "acc_move": am, "acc_swap": asw, "final_slots": fin,
+            "round_trips": int(trips[0]) if want_trips else None}
 
 
 def simplified_energy_hist(variant: int, n: int) -> np.ndarray:

@@ -39,7 +39,9 @@
  *                            its published definition.
  *   orc_pt_run            -- Algorithm 2 (Sec. 3): parallel tempering over the
  *                            simplified problem, energy = number of empty bins,
- *                            Metropolis moves and neighbour exchanges.
+ *                            Metropolis moves and neighbour exchanges;
+ *                            orc_pt_run_trips also counts the round trips of
+ *                            configurations between the ends of the ladder.
  *   orc_simplified_energy_hist -- exhaustive enumeration of the simplified
  *                            problem of Sec. 3 (every pair k at any of its
  *                            start slots): the number N(E) of configurations
@@ -514,6 +516,8 @@ typedef struct {
     int slot[ORC_MAXN + 1];           /* start bin (0-based) of pair k */
     int occ[ORC_MAXSPAN];             /* balls per bin */
     int E;                            /* number of empty bins */
+    int dir;                          /* the last end of the ladder it sat at: 0 none
+                                         yet, 1 rung 0 (beta = 0), 2 rung M-1 */
 } pt_conf;
 
 static void conf_recount(pt_conf *c, int n, const int *d, int bins)
@@ -527,11 +531,18 @@ static void conf_recount(pt_conf *c, int n, const int *d, int bins)
 /* hist: M x (2n+1) counts of E per rung (temperature index) after burn-in.
  * acc_move[M], acc_swap[M]: accepted moves per rung, accepted exchanges per
  * lower rung of a pair (both may be NULL).  final_slots: L x M x n start slots
- * at the end, per ladder and temperature (may be NULL).
+ * at the end, per ladder and temperature (may be NULL).  round_trips (may be
+ * NULL): how often, over all ladders, a configuration came back to rung 0
+ * after reaching rung M-1 since it was last at rung 0 -- a walk from the
+ * hottest end of the ladder to the coldest and back, the usual measure of
+ * how well the exchanges carry configurations through the temperatures.  Each
+ * iteration first looks at the configurations at the two ends (rung 0: count
+ * a return if it had reached rung M-1, then mark it; rung M-1: mark it if it
+ * came from rung 0); returns are counted from iteration `burnin` on.
  * Variants 0 (Skolem) and 1 (Langford) only: bins are the 2n positions. */
-int orc_pt_run(int variant, int n, int M, const double *beta, int L, uint64_t iters,
-               uint64_t burnin, uint64_t seed, uint64_t *hist, uint64_t *acc_move,
-               uint64_t *acc_swap, uint8_t *final_slots)
+int orc_pt_run_trips(int variant, int n, int M, const double *beta, int L, uint64_t iters,
+                     uint64_t burnin, uint64_t seed, uint64_t *hist, uint64_t *acc_move,
+                     uint64_t *acc_swap, uint8_t *final_slots, uint64_t *round_trips)
 {
     if (variant < 0 || variant > 1 || n < 2 || n > ORC_MAXN || M < 1 || M > 64 || L < 1)
         return -1;
@@ -558,6 +569,7 @@ int orc_pt_run(int variant, int n, int M, const double *beta, int L, uint64_t it
     memset(hist, 0, sizeof(uint64_t) * (size_t)M * (bins + 1));
     if (acc_move) memset(acc_move, 0, sizeof(uint64_t) * (size_t)M);
     if (acc_swap) memset(acc_swap, 0, sizeof(uint64_t) * (size_t)M);
+    if (round_trips) *round_trips = 0;
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
 
     for (int l = 0; l < L; l++) {
@@ -568,8 +580,14 @@ int orc_pt_run(int variant, int n, int M, const double *beta, int L, uint64_t it
                 conf[j].slot[k] = (int)(((uint64_t)r[0] * (uint64_t)nslot[k]) >> 32);
             }
             conf_recount(&conf[j], n, d, bins);
+            conf[j].dir = 0;
         }
         for (uint64_t t = 0; t < iters; t++) {
+            if (M >= 2) {                             /* the ends of the ladder */
+                if (conf[0].dir == 2 && t >= burnin && round_trips) (*round_trips)++;
+                conf[0].dir = 1;
+                if (conf[M - 1].dir == 1) conf[M - 1].dir = 2;
+            }
             if (t >= burnin)                          /* Ratio(j) statistics */
                 for (int j = 0; j < M; j++) hist[j * (bins + 1) + conf[j].E]++;
             for (int j = 0; j < M; j++) {             /* Metropolis moves */
@@ -622,6 +640,14 @@ int orc_pt_run(int variant, int n, int M, const double *beta, int L, uint64_t it
     free(tswap);
     free(conf);
     return 0;
+}
+
+int orc_pt_run(int variant, int n, int M, const double *beta, int L, uint64_t iters,
+               uint64_t burnin, uint64_t seed, uint64_t *hist, uint64_t *acc_move,
+               uint64_t *acc_swap, uint8_t *final_slots)
+{
+    return orc_pt_run_trips(variant, n, M, beta, L, iters, burnin, seed, hist, acc_move,
+                            acc_swap, final_slots, NULL);
 }
 
 /* ------------------------------ O4: exact energy counts, tiny problems */

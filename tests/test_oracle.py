@@ -292,3 +292,48 @@ def test_pt_deterministic_and_seed_dependent():
     # each state's slots are legal start bins
     d = [k for k in range(1, 6)]
     assert np.all(a["final_slots"] < np.array([10 - dk for dk in d]))
+
+
+def _zigzag_bounds(M, T):
+    # With every exchange accepted (equal temperatures) the positions follow
+    # the brick-wall permutation: each configuration walks to one end, waits
+    # one iteration there, walks back, a zigzag of period 2M; so a ladder of
+    # M configurations completes T / 2 round trips over T iterations, up to
+    # one partial trip per configuration at each end of the run.
+    return T // 2 - M - 2, T // 2 + 1
+
+
+@pytest.mark.parametrize("M,T,burnin", [(2, 3, 0), (2, 4, 0), (2, 7, 0), (2, 200, 0), (2, 200, 51)])
+def test_pt_round_trips_two_rungs_closed_form(M, T, burnin):
+    # Two rungs at the same temperature: the pair (0, 1) is exchanged at every
+    # even iteration, so the configurations trade places every two
+    # iterations; the first return to rung 0 after visiting rung 1 is seen at
+    # iteration 3, then one at every odd iteration.
+    beta = [1.0, 1.0]
+    r = oracle.pt_run(SK, 5, beta, 1, T, burnin, 3, want_trips=True)
+    want = len([t for t in range(max(3, burnin), T) if t % 2 == 1])
+    assert r["round_trips"] == want
+
+
+@pytest.mark.parametrize("M", [1, 3, 5, 8])
+def test_pt_round_trips_equal_temperatures(M):
+    T, L = 1000, 3
+    r = oracle.pt_run(LA, 6, [0.7] * M, L, T, 0, 9, want_trips=True)
+    if M == 1:
+        assert r["round_trips"] == 0
+        return
+    lo, hi = _zigzag_bounds(M, T)
+    assert L * lo <= r["round_trips"] <= L * hi, (M, r["round_trips"])
+    # counting the trips changes nothing else
+    q = oracle.pt_run(LA, 6, [0.7] * M, L, T, 0, 9)
+    assert np.array_equal(q["hist"], r["hist"]) and np.array_equal(q["acc_swap"], r["acc_swap"])
+    assert q["round_trips"] is None
+
+
+def test_pt_round_trips_frozen_ladder():
+    # Temperatures so far apart that no exchange is ever accepted once the
+    # cold rungs sit at low energy: nearly no configuration travels, far
+    # below the zigzag's T / 2 per ladder.
+    T = 2000
+    r = oracle.pt_run(SK, 8, [0.0, 60.0, 120.0], 2, T, T // 2, 5, want_trips=True)
+    assert r["round_trips"] < 0.05 * T
