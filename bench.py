@@ -549,8 +549,9 @@ def run_pt_large_bench(args, sk, sh):
         rows = []
         for budget in args.pt_budgets:
             est, rep = sk.pt_estimate(v, n, budget, rungs=args.pt_rungs, ladders=4096, seed=budget,
-                                      stream=sh)
+                                      stream=sh, round_trips=True)
             rows.append({"iterations": budget, "rungs": rep["rungs"], "estimate": est,
+                         "round_trips_per_configuration": rep["round_trips"] / (4096 * rep["rungs"]),
                          "rel_error": (est / exact - 1) if exact else None,
                          "paper_estimate": paper,
                          "paper_rel_error": (paper / exact - 1) if exact else None,
@@ -650,7 +651,8 @@ def run_pt_bias_bench(args, sk, sh):
     32-rung ladder topped at beta_max = 32, 48 and 64, and with beta_max = 32
     and four times the iterations; per run the estimate and its standard
     error (16 groups of 256 ladders), the smallest exchange acceptance of
-    the ladder and P(E = 0) at the top rung (the last ratio of Algorithm 2).
+    the ladder, P(E = 0) at the top rung (the last ratio of Algorithm 2) and
+    the round trips of configurations between the ends of the ladder.
     Then 64 rungs topped at beta_max = 32 (two warps a ladder): the same
     top temperature with twice the rungs, closer neighbours and higher
     exchange acceptance.  With --pt-rungs 64 only the 64-rung ladder runs,
@@ -670,9 +672,11 @@ def run_pt_bias_bench(args, sk, sh):
         rows = []
         for bmax, budget, rungs in variants:
             est, rep = sk.pt_estimate(v, n, budget, rungs=rungs, ladders=4096, seed=7,
-                                      beta_max=bmax, stream=sh)
+                                      beta_max=bmax, stream=sh, round_trips=True)
             M = rep["rungs"]
             rows.append({"beta_max": bmax, "iterations": budget, "rungs": M, "estimate": est,
+                         "round_trips": rep["round_trips"],
+                         "round_trips_per_configuration": rep["round_trips"] / (4096 * M),
                          "rel_stderr": rep["rel_stderr"],
                          "rel_error": (est / exact - 1) if exact else None,
                          "z_vs_exact": ((est / exact - 1) / rep["rel_stderr"]) if exact else None,

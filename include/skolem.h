@@ -275,6 +275,8 @@ typedef struct sk_pt_opts {
   int proposal;           /* SK_PT_PLAIN (default) or SK_PT_LEARNED */
   const void *model;      /* SK_PT_LEARNED: a model from sk_mlp_create */
   void *stream;           /* cudaStream_t or NULL */
+  int round_trips;        /* nonzero: count round trips (SK_PT_PLAIN; a few
+                             percent more kernel time) */
 } sk_pt_opts;
 
 typedef struct sk_pt_report {
@@ -293,6 +295,11 @@ typedef struct sk_pt_report {
    * that has not equilibrated.  0 with fewer than 2 groups (ladders < 2) and
    * for the learned proposal; NaN when the group estimates average to 0. */
   double rel_stderr;
+  /* With opts->round_trips: how often, over all ladders and after burn-in,
+   * a configuration came back to rung 0 having reached rung M-1 since it was
+   * last there (a trip from the hottest end of the ladder to the coldest and
+   * back); 0 otherwise. */
+  uint64_t round_trips;
 } sk_pt_report;
 
 /* Approximate count by parallel tempering (Sec. 3, Algorithm 2): budget =
@@ -317,6 +324,18 @@ int pt_estimate_ex(int variant, int n, uint64_t budget, const sk_pt_opts *opts, 
 int sk_pt_run(int variant, int n, int M, const double *beta, int L, uint64_t iters,
               uint64_t burnin, uint64_t seed, uint64_t *hist, uint64_t *acc_move,
               uint64_t *acc_swap, uint8_t *final_slots);
+
+/* sk_pt_run that also counts round trips along the ladder: round_trips
+ * (host, one value, required) = how often, over all ladders, a configuration
+ * came back to rung 0 having reached rung M-1 since it was last at rung 0.
+ * Each iteration first looks at the configurations at the two ends (at rung
+ * 0: count a return if it had reached rung M-1, then mark it as at rung 0;
+ * at rung M-1: mark it if it came from rung 0); returns are counted from
+ * iteration `burnin` on.  The other outputs are those of sk_pt_run, bit for
+ * bit. */
+int sk_pt_run_trips(int variant, int n, int M, const double *beta, int L, uint64_t iters,
+                    uint64_t burnin, uint64_t seed, uint64_t *hist, uint64_t *acc_move,
+                    uint64_t *acc_swap, uint8_t *final_slots, uint64_t *round_trips);
 
 /* The estimator of pt_estimate on host histograms; host code only, no device
  * needed.  hist: `groups` >= 1 histograms of M x (2n+1) energy counts (groups x

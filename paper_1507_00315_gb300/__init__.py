@@ -136,7 +136,8 @@ class PtOpts(ctypes.Structure):
     _fields_ = [("rungs", ctypes.c_int), ("ladders", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("burnin_frac", ctypes.c_double), ("beta", ctypes.POINTER(ctypes.c_double)),
                 ("beta_max", ctypes.c_double), ("proposal", ctypes.c_int),
-                ("model", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
+                ("model", ctypes.c_void_p), ("stream", ctypes.c_void_p),
+                ("round_trips", ctypes.c_int)]
 
 
 class PtReport(ctypes.Structure):
@@ -147,7 +148,7 @@ class PtReport(ctypes.Structure):
                 ("acc_swap", ctypes.c_double * PT_MAX_RUNGS),
                 ("estimate", ctypes.c_double), ("kernel_ms", ctypes.c_double),
                 ("tune_ms", ctypes.c_double), ("wall_ms", ctypes.c_double),
-                ("rel_stderr", ctypes.c_double)]
+                ("rel_stderr", ctypes.c_double), ("round_trips", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         M = self.rungs
@@ -155,7 +156,8 @@ class PtReport(ctypes.Structure):
                 "burnin": self.burnin, "beta": list(self.beta[:M]), "ratio": list(self.ratio[:M]),
                 "acc_move": list(self.acc_move[:M]), "acc_swap": list(self.acc_swap[:M]),
                 "estimate": self.estimate, "kernel_ms": self.kernel_ms,
-                "tune_ms": self.tune_ms, "wall_ms": self.wall_ms, "rel_stderr": self.rel_stderr}
+                "tune_ms": self.tune_ms, "wall_ms": self.wall_ms, "rel_stderr": self.rel_stderr,
+                "round_trips": self.round_trips}
 
 _lib = None
 
@@ -210,6 +212,7 @@ def lib():
                                      ctypes.POINTER(PtReport)]
         L.sk_pt_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, u64, u64,
                                 u64, vp, vp, vp, vp]
+        L.sk_pt_run_trips.argtypes = L.sk_pt_run.argtypes + [vp]
         L.sk_pt_run_learned.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int,
                                         u64, u64, u64, vp, vp, vp, vp]
         L.sk_pt_tune_ladder.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -476,9 +479,10 @@ def _np():
 
 
 def pt_run(variant, n: int, beta, ladders: int, iters: int, burnin: int, seed: int,
-           want_final: bool = False, model=None):
-    """sk_pt_run (or sk_pt_run_learned with a model): dict(hist[M, 2n+1],
-    acc_move[M], acc_swap[M], final_slots[L, M, n] or None)."""
+           want_final: bool = False, model=None, want_trips: bool = False):
+    """sk_pt_run (sk_pt_run_trips with want_trips, sk_pt_run_learned with a
+    model): dict(hist[M, 2n+1], acc_move[M], acc_swap[M], final_slots[L, M, n]
+    or None, round_trips or None)."""
     np = _np()
     beta = np.ascontiguousarray(beta, dtype=np.float64)
     M = beta.shape[0]
@@ -492,12 +496,18 @@ def pt_run(variant, n: int, beta, ladders: int, iters: int, burnin: int, seed: i
         fin = None
     else:
         fin = np.zeros((ladders, M, n), dtype=np.uint8) if want_final else None
-        st = lib().sk_pt_run(_variant(variant), n, M, beta.ctypes.data, ladders, iters, burnin, seed,
-                             hist.ctypes.data, am.ctypes.data, asw.ctypes.data,
-                             fin.ctypes.data if fin is not None else None)
+        args = (_variant(variant), n, M, beta.ctypes.data, ladders, iters, burnin, seed,
+                hist.ctypes.data, am.ctypes.data, asw.ctypes.data,
+                fin.ctypes.data if fin is not None else None)
+        if want_trips:
+            trips = np.zeros(1, dtype=np.uint64)
+            st = lib().sk_pt_run_trips(*args, trips.ctypes.data)
+        else:
+            st = lib().sk_pt_run(*args)
     if st != SK_OK:
         raise SkolemError(st, "sk_pt_run")
-    return {"hist": hist, "acc_move": am, "acc_swap": asw, "final_slots": fin}
+    return {"hist": hist, "acc_move": am, "acc_swap": asw, "final_slots": fin,
+            "round_trips": int(trips[0]) if want_trips and model is None else None}
 
 
 def pt_estimate_hist(variant, n: int, beta, hist):
@@ -531,7 +541,8 @@ def tune_ladder(variant, n: int, rungs: int = 32, beta_max: float = 32.0, seed: 
 
 
 def pt_estimate(variant, n: int, budget: int, rungs=0, ladders=0, seed=0, burnin_frac=0.0,
-                beta=None, beta_max=0.0, model=None, stream=None, proposal=None):
+                beta=None, beta_max=0.0, model=None, stream=None, proposal=None,
+                round_trips=False):
     """pt_estimate_ex: (estimate, report dict).  proposal defaults to PT_LEARNED
     with a model, else PT_PLAIN."""
     np = _np()
@@ -547,6 +558,7 @@ def pt_estimate(variant, n: int, budget: int, rungs=0, ladders=0, seed=0, burnin
         o.model = model.handle
     if proposal is not None:
         o.proposal = proposal
+    o.round_trips = 1 if round_trips else 0
     o.stream = stream
     out = ctypes.c_double()
     rep = PtReport()

@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256)
     mlp_loss_kernel(const float* __restrict__ Z, int ldz, const unsigned char* __restrict__ slots,
                     int B, MoveTable mt, float beta_star, float inv_B, __nv_bfloat16* dZ,
                     float* loss) {
-  __shared__ unsigned char s_occ[8][2 * kPtMaxN];
+  __shared__ int s_occ[8][2 * kPtMaxN];
   __shared__ unsigned char s_slot[8][kPtMaxN + 1];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int b = blockIdx.x * 8 + w;
@@ -127,13 +127,11 @@ __global__ void __launch_bounds__(256)
   const int n = mt.n, bins = 2 * n;
   for (int i = lane; i < bins; i += 32) s_occ[w][i] = 0;
   __syncwarp();
-  if (lane == 0) {
-    for (int k = 1; k <= n; ++k) {
-      const int s = slots[(size_t)b * n + (k - 1)];
-      s_slot[w][k] = (unsigned char)s;
-      s_occ[w][s] += 1;
-      s_occ[w][s + k + mt.delta] += 1;
-    }
+  for (int k = 1 + lane; k <= n; k += 32) {           // lane k-1 places pair k
+    const int s = slots[(size_t)b * n + (k - 1)];
+    s_slot[w][k] = (unsigned char)s;
+    atomicAdd(&s_occ[w][s], 1);
+    atomicAdd(&s_occ[w][s + k + mt.delta], 1);
   }
   __syncwarp();
   const float* z = Z + (size_t)b * ldz;

@@ -31,6 +31,8 @@ struct PtLane {
   unsigned short* hist;                 // [E][C]
   unsigned char* slot;                  // [k][C], k = 1..n
   unsigned char* occ;                   // [b][C]
+  unsigned char* dir;                   // [C]: the last end of the ladder each column's
+                                        // configuration sat at (0 none, 1 rung 0, 2 rung M-1)
   unsigned long long tm1, tm2;          // move thresholds at this lane's rung, dE = 1, 2
   const unsigned long long* tswap;      // [M][bins+1]
   int rung, M, n, delta, bins, nb;
@@ -49,11 +51,25 @@ struct PtLane {
 // or exchange is rejected.  With two warps a ladder, the pair (31, 32) is
 // exchanged through shared memory on odd iterations, after a barrier of the
 // two warps (also the point where the columns that change warp become the
-// other warp's).
-template <int W>
+// other warp's).  TRIPS: first the lanes at the two ends of the ladder look
+// at their configurations -- at rung 0 a configuration that has reached rung
+// M-1 since it was last there completes a round trip (counted from `burnin`
+// on), at rung M-1 one that came from rung 0 is marked.
+template <int W, bool TRIPS>
 __device__ __forceinline__ void pt_step(const PtLane& S, const uint4 wc, const unsigned t, int& c,
-                                        int& E, unsigned& accm, unsigned& accs) {
+                                        int& E, unsigned& accm, unsigned& accs, unsigned& trips) {
   constexpr int C = 32 * W;
+  if constexpr (TRIPS) {
+    if (S.rung == 0 || S.rung == S.M - 1) {
+      const int dv = S.dir[c];
+      if (S.rung == 0) {
+        trips += (unsigned)(dv == 2 && t >= S.burnin);
+        S.dir[c] = 1;
+      } else if (dv == 1) {
+        S.dir[c] = 2;
+      }
+    }
+  }
   unsigned xw_lo = __shfl_up_sync(0xffffffffu, wc.w, 1);          // word 3 of rung - 1
   S.hist[E * C + S.rung] += (unsigned short)(S.active && t >= S.burnin);
   // Metropolis move: pair k to another start slot
@@ -126,12 +142,15 @@ __device__ __forceinline__ void pt_step(const PtLane& S, const uint4 wc, const u
 // statistics of every rung (after burn-in), one Metropolis move per
 // configuration, then the exchanges of the pairs (j, j+1) with j = t mod 2.
 // Lane j of warp h serves rung 32 h + j (see sk_pt.cuh): it holds the column
-// c of the configuration now at that rung and its energy E.
-template <int W>
+// c of the configuration now at that rung and its energy E.  TRIPS: the
+// round trips of the configurations between the ends of the ladder are
+// counted into *trips_g.
+template <int W, bool TRIPS>
 __global__ void __launch_bounds__(128, 7)
     pt_kernel(PtParams p, const unsigned long long* __restrict__ tmove_g,
               const unsigned long long* __restrict__ tswap_g, unsigned long long* hist_g,
-              unsigned long long* accm_g, unsigned long long* accs_g, unsigned char* final_slots) {
+              unsigned long long* accm_g, unsigned long long* accs_g, unsigned char* final_slots,
+              unsigned long long* trips_g) {
   constexpr int C = 32 * W;
   extern __shared__ __align__(16) unsigned char pt_smem[];
   __shared__ unsigned xslot[2][6];                    // W = 2: per ladder of the block
@@ -144,6 +163,7 @@ __global__ void __launch_bounds__(128, 7)
   S.hist = (unsigned short*)wbase;
   S.slot = wbase + pt_hist_bytes(n, W);
   S.occ = S.slot + (n + 1) * C;
+  S.dir = S.occ + bins * C;
   S.rung = rung;
   S.M = M;
   S.n = n;
@@ -166,9 +186,10 @@ __global__ void __launch_bounds__(128, 7)
     for (int e = 0; e < nb; ++e) hist[e * C + rung] = 0;
     for (int b = 0; b < bins; ++b) occ[b * C + rung] = 0;
     for (int k = 0; k <= n; ++k) slot[k * C + rung] = 0;
+    S.dir[rung] = 0;
     // column `rung` <- the configuration that starts at that rung
     int c = rung, E = 0;
-    unsigned accm = 0, accs = 0;
+    unsigned accm = 0, accs = 0, trips = 0;
     if (active) {
       for (int k = 1; k <= n; ++k) {
         const unsigned L = (unsigned)(bins - (k + p.delta));
@@ -190,11 +211,11 @@ __global__ void __launch_bounds__(128, 7)
       unsigned t = (unsigned)t0;
       for (; t + 1 < t1; t += 2) {
         const uint4 wb = philox4x32_10_rk(make_uint4(t + 1u, (unsigned)rung, (unsigned)ladder, 2u), p.rk);
-        pt_step<W>(S, wa, t, c, E, accm, accs);
+        pt_step<W, TRIPS>(S, wa, t, c, E, accm, accs, trips);
         wa = philox4x32_10_rk(make_uint4(t + 2u, (unsigned)rung, (unsigned)ladder, 2u), p.rk);
-        pt_step<W>(S, wb, t + 1, c, E, accm, accs);
+        pt_step<W, TRIPS>(S, wb, t + 1, c, E, accm, accs, trips);
       }
-      if (t < t1) pt_step<W>(S, wa, t, c, E, accm, accs);
+      if (t < t1) pt_step<W, TRIPS>(S, wa, t, c, E, accm, accs, trips);
       if (t1 < p.iters && active) {                // 16-bit counters: flush this rung's column
         unsigned long long* hist_l =
             hist_g + (size_t)pt_group(ladder, p.ladders, p.groups) * M * nb;
@@ -214,6 +235,7 @@ __global__ void __launch_bounds__(128, 7)
       }
       if (accm) atomicAdd(&accm_g[rung], (unsigned long long)accm);
       if (accs) atomicAdd(&accs_g[rung], (unsigned long long)accs);
+      if (TRIPS && trips) atomicAdd(trips_g, (unsigned long long)trips);
       if (final_slots)
         for (int k = 1; k <= n; ++k)
           final_slots[((size_t)ladder * M + rung) * n + (k - 1)] = slot[k * C + c];
@@ -256,11 +278,13 @@ int pt_check(int variant, int n, int M, const double* beta, int L) {
 
 // Runs L ladders for `iters` iterations; host outputs as in the header.
 // With groups > 1 the histograms are also kept per group of ladders
-// (group_hist: groups x M x (2n+1), host), hist being their sum.
+// (group_hist: groups x M x (2n+1), host), hist being their sum.  With
+// round_trips (host, one value) the kernel also counts the round trips of
+// the configurations between the ends of the ladder.
 int pt_run_impl(int variant, int n, int M, const double* beta, int L, uint64_t iters,
                 uint64_t burnin, uint64_t seed, uint64_t* hist, uint64_t* accm, uint64_t* accs,
                 uint8_t* final_slots, void* stream, double* kernel_ms, int groups = 1,
-                uint64_t* group_hist = nullptr) {
+                uint64_t* group_hist = nullptr, uint64_t* round_trips = nullptr) {
   int st = pt_check(variant, n, M, beta, L);
   if (st) return st;
   if (!hist || iters > 0xffffffffULL || groups < 1 || groups > L || (groups > 1 && !group_hist))
@@ -294,7 +318,7 @@ int pt_run_impl(int variant, int n, int M, const double* beta, int L, uint64_t i
   }
   p.groups = groups;
   const size_t n_hist = (size_t)groups * M * nb, n_fin = final_slots ? (size_t)L * M * n : 0;
-  const size_t bytes = (tm.size() + ts.size() + n_hist + 2 * (size_t)M) * 8 + n_fin;
+  const size_t bytes = (tm.size() + ts.size() + n_hist + 2 * (size_t)M + 1) * 8 + n_fin;
   cudaStream_t s = (cudaStream_t)stream;
   bool own = false;
   if (!s) {
@@ -312,13 +336,16 @@ int pt_run_impl(int variant, int n, int M, const double* beta, int L, uint64_t i
   unsigned long long* dh = dts + ts.size();
   unsigned long long* dam = dh + n_hist;
   unsigned long long* das = dam + M;
-  unsigned char* dfin = final_slots ? (unsigned char*)(das + M) : nullptr;
+  unsigned long long* dtrips = das + M;
+  unsigned char* dfin = final_slots ? (unsigned char*)(dtrips + 1) : nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   e = cudaMemcpyAsync(dtm, tm.data(), tm.size() * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dts, ts.data(), ts.size() * 8, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(dh, 0, (n_hist + 2 * (size_t)M) * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dh, 0, (n_hist + 2 * (size_t)M + 1) * 8, s);
   const size_t smem = pt_smem_bytes(n, W, p.warps_per_block);
-  const auto kernel = W == 2 ? pt_kernel<2> : pt_kernel<1>;
+  const bool trips = round_trips != nullptr;
+  const auto kernel = W == 2 ? (trips ? pt_kernel<2, true> : pt_kernel<2, false>)
+                             : (trips ? pt_kernel<1, true> : pt_kernel<1, false>);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, sms = 0, per_sm = 0;
@@ -334,11 +361,11 @@ int pt_run_impl(int variant, int n, int M, const double* beta, int L, uint64_t i
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e == cudaSuccess) e = cudaEventRecord(e0, s);
   if (e == cudaSuccess) {
-    kernel<<<grid, 32 * p.warps_per_block, smem, s>>>(p, dtm, dts, dh, dam, das, dfin);
+    kernel<<<grid, 32 * p.warps_per_block, smem, s>>>(p, dtm, dts, dh, dam, das, dfin, dtrips);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-  std::vector<unsigned long long> hh(n_hist + 2 * (size_t)M);
+  std::vector<unsigned long long> hh(n_hist + 2 * (size_t)M + 1);
   if (e == cudaSuccess) e = cudaMemcpyAsync(hh.data(), dh, hh.size() * 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && final_slots)
     e = cudaMemcpyAsync(final_slots, dfin, n_fin, cudaMemcpyDeviceToHost, s);
@@ -362,6 +389,7 @@ int pt_run_impl(int variant, int n, int M, const double* beta, int L, uint64_t i
     if (accm) accm[j] = hh[n_hist + j];
     if (accs) accs[j] = hh[n_hist + M + j];
   }
+  if (round_trips) *round_trips = hh[n_hist + 2 * (size_t)M];
   if (kernel_ms) *kernel_ms = ms;
   return SK_OK;
 }
@@ -439,6 +467,15 @@ extern "C" int sk_pt_run(int variant, int n, int M, const double* beta, int L, u
                          uint64_t* acc_swap, uint8_t* final_slots) {
   return sk::pt_run_impl(variant, n, M, beta, L, iters, burnin, seed, hist, acc_move, acc_swap,
                          final_slots, nullptr, nullptr);
+}
+
+extern "C" int sk_pt_run_trips(int variant, int n, int M, const double* beta, int L,
+                               uint64_t iters, uint64_t burnin, uint64_t seed, uint64_t* hist,
+                               uint64_t* acc_move, uint64_t* acc_swap, uint8_t* final_slots,
+                               uint64_t* round_trips) {
+  if (!round_trips) return SK_EINVAL;
+  return sk::pt_run_impl(variant, n, M, beta, L, iters, burnin, seed, hist, acc_move, acc_swap,
+                         final_slots, nullptr, nullptr, 1, nullptr, round_trips);
 }
 
 namespace sk {
@@ -524,9 +561,12 @@ int pt_estimate_impl(int variant, int n, uint64_t budget, const sk_pt_opts* o, d
   if (proposal == SK_PT_LEARNED)
     st = pt_learned_run(variant, n, M, beta.data(), L, budget, burnin, seed, o->model, hist.data(),
                         am.data(), as.data(), o ? o->stream : nullptr, &kms);
-  else
+  uint64_t trips = 0;
+  const bool want_trips = o && o->round_trips && proposal == SK_PT_PLAIN;
+  if (proposal == SK_PT_PLAIN)
     st = pt_run_impl(variant, n, M, beta.data(), L, budget, burnin, seed, hist.data(), am.data(),
-                     as.data(), nullptr, o ? o->stream : nullptr, &kms, groups, ghist.data());
+                     as.data(), nullptr, o ? o->stream : nullptr, &kms, groups, ghist.data(),
+                     want_trips ? &trips : nullptr);
   if (st) return st;
   double ratios[kPtMaxRungs];
   double rel_se = 0.0;
@@ -549,6 +589,7 @@ int pt_estimate_impl(int variant, int n, uint64_t budget, const sk_pt_opts* o, d
     }
     rep->estimate = est;
     rep->rel_stderr = rel_se;
+    rep->round_trips = trips;
     rep->kernel_ms = kms;
     rep->tune_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     rep->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

@@ -77,15 +77,15 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const unsigned* rk) {
 
 // Shared-memory layout of one ladder of W warps (32 W columns): the energy
 // histogram ([E][rung] 16-bit counters, flushed to global memory every
-// kPtFlush iterations), then the start slots ([k][column]) and bin
-// occupancies ([b][column]), one byte an entry.  Thresholds stay in
+// kPtFlush iterations), then the start slots ([k][column]), bin occupancies
+// ([b][column]) and the round-trip marks ([column]), one byte an entry.  Thresholds stay in
 // registers (moves) and global memory, L1-cached (exchanges).
 constexpr unsigned kPtFlush = 32768;
 __host__ __device__ inline size_t pt_hist_bytes(int n, int W) {
   return ((size_t)(2 * n + 1) * 32 * W * 2 + 15) / 16 * 16;
 }
 __host__ __device__ inline size_t pt_ladder_bytes(int n, int W) {
-  const size_t st = (size_t)(n + 1) * 32 * W + (size_t)(2 * n) * 32 * W;
+  const size_t st = (size_t)(n + 1) * 32 * W + (size_t)(2 * n) * 32 * W + (size_t)32 * W;
   return (pt_hist_bytes(n, W) + st + 15) / 16 * 16;
 }
 __host__ __device__ inline size_t pt_smem_bytes(int n, int W, int wpb) {

@@ -98,11 +98,14 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes, int lan
 
 // A chain's logit row (bf16) held in registers: chunk c of 256 moves, lane l
 // holds moves 256 c + 8 l .. + 7 in one 16-byte word.  Lanes whose 8 moves
-// all lie beyond NM load nothing (their words are never used).
+// all lie beyond NM load nothing (their words are never used).  CH = the
+// chunks of the move table, ceil(NM / 256): the kernels are compiled for
+// each CH up to kLtChunks, so no lane walks chunks the problem does not have.
 constexpr int kLtChunks = kMaxMoves / 256;
+template <int CH>
 struct LogitRow {
-  uint4 w[kLtChunks];
-  unsigned valid[kLtChunks];   // bit i: move 256 c + 8 l + i is a valid move of the state
+  uint4 w[CH];
+  unsigned valid[CH];          // bit i: move 256 c + 8 l + i is a valid move of the state
 };
 
 __device__ __forceinline__ float bf16_lo(unsigned x) { return __uint_as_float(x << 16); }
@@ -112,19 +115,21 @@ __device__ __forceinline__ float row_elem(const uint4& w, int i) {
   return (i & 1) ? bf16_hi(x) : bf16_lo(x);
 }
 
-__device__ __forceinline__ void load_row(const __nv_bfloat16* z, int NM, int lane, LogitRow& r) {
+template <int CH>
+__device__ __forceinline__ void load_row(const __nv_bfloat16* z, int NM, int lane, LogitRow<CH>& r) {
 #pragma unroll
-  for (int c = 0; c < kLtChunks; ++c) {
+  for (int c = 0; c < CH; ++c) {
     const int m0 = c * 256 + lane * 8;
     r.w[c] = m0 < NM ? __ldg((const uint4*)(z + m0)) : make_uint4(0, 0, 0, 0);
   }
 }
 
 // Valid-move bits of the state in s_slot for the row's layout.
+template <int CH>
 __device__ __forceinline__ void row_valid(const MoveMaps& mm, const unsigned char* s_slot, int NM,
-                                          int lane, LogitRow& r) {
+                                          int lane, LogitRow<CH>& r) {
 #pragma unroll
-  for (int c = 0; c < kLtChunks; ++c) {
+  for (int c = 0; c < CH; ++c) {
     const int m0 = c * 256 + lane * 8;
     unsigned bits = 0;
     if (m0 < NM) {
@@ -144,10 +149,11 @@ __device__ __forceinline__ void row_valid(const MoveMaps& mm, const unsigned cha
 // log sum exp of the row over its valid moves, in one pass over the
 // registers: each lane keeps a running maximum and the sum scaled to it
 // (rescaled when the maximum grows), then the lanes' pairs are combined.
-__device__ __forceinline__ float row_lse(const LogitRow& r) {
+template <int CH>
+__device__ __forceinline__ float row_lse(const LogitRow<CH>& r) {
   float mx = -INFINITY, sum = 0.f;
 #pragma unroll
-  for (int c = 0; c < kLtChunks; ++c)
+  for (int c = 0; c < CH; ++c)
 #pragma unroll
     for (int i = 0; i < 8; ++i)
       if ((r.valid[c] >> i) & 1u) {
@@ -193,7 +199,8 @@ __global__ void lt_init_kernel(LearnedDev d) {
 }
 
 // After a forward pass of the current states: keep their logits and lse.
-__global__ void __launch_bounds__(256, 2) lt_keep_kernel(LearnedDev d, MoveTable mt,
+template <int CH>
+__global__ void __launch_bounds__(256, CH <= 4 ? 4 : 2) lt_keep_kernel(LearnedDev d, MoveTable mt,
                                                       const __nv_bfloat16* Z) {
   __shared__ MoveMaps mm;
   __shared__ unsigned char s_slot[8][kPtMaxN + 8];
@@ -202,13 +209,13 @@ __global__ void __launch_bounds__(256, 2) lt_keep_kernel(LearnedDev d, MoveTable
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int c = blockIdx.x * 8 + w; c < d.B; c += gridDim.x * 8) {
     load_state(d.slots + (size_t)c * d.n, d.n, d.delta, s_slot[w], nullptr, lane);
-    LogitRow r;
+    LogitRow<CH> r;
     load_row(Z + (size_t)c * d.NMp, mt.NM, lane, r);
     row_valid(mm, s_slot[w], mt.NM, lane, r);
     const float l = row_lse(r);
     __nv_bfloat16* zc = d.Zcur + (size_t)c * d.NMp;
 #pragma unroll
-    for (int k = 0; k < kLtChunks; ++k)
+    for (int k = 0; k < CH; ++k)
       if (k * 256 + lane * 8 < mt.NM) *(uint4*)(zc + k * 256 + lane * 8) = r.w[k];
     if (lane == 0) d.lse[c] = l;
     __syncwarp();
@@ -221,7 +228,8 @@ __global__ void __launch_bounds__(256, 2) lt_keep_kernel(LearnedDev d, MoveTable
 // registers: the chunk sums (warp reductions), the chunk that holds u *
 // total, a scan of its lanes' sums, then the lane that holds it walks its 8
 // moves.
-__global__ void __launch_bounds__(256, 2) lt_propose_kernel(LearnedDev d, MoveTable mt, unsigned t,
+template <int CH>
+__global__ void __launch_bounds__(256, CH <= 4 ? 4 : 2) lt_propose_kernel(LearnedDev d, MoveTable mt, unsigned t,
                                                          int count_stats,
                                                          unsigned char* prop_slots) {
   __shared__ MoveMaps mm;
@@ -237,7 +245,7 @@ __global__ void __launch_bounds__(256, 2) lt_propose_kernel(LearnedDev d, MoveTa
       prefetch_l2(d.Zcur + (size_t)cn * d.NMp, (size_t)NM * 2, lane);
       prefetch_l2(d.slots + (size_t)cn * d.n, (size_t)d.n, lane);
     }
-    LogitRow r;
+    LogitRow<CH> r;
     load_row(d.Zcur + (size_t)c * d.NMp, NM, lane, r);
     const int ladder = c / d.M, rg = d.rung[c], E = d.E[c];
     if (lane == 0 && count_stats) d.hist[((size_t)ladder * d.M + rg) * d.nb + E] += 1;
@@ -246,10 +254,10 @@ __global__ void __launch_bounds__(256, 2) lt_propose_kernel(LearnedDev d, MoveTa
     const float lse = d.lse[c];
     const uint4 rw = philox4x32_10(make_uint4(t, (unsigned)rg, (unsigned)ladder, 5u), d.key0, d.key1);
     // per lane and chunk: the sum of exp(z - lse) over its valid moves
-    float part[kLtChunks], csum[kLtChunks];
+    float part[CH], csum[CH];
     float total = 0.f;
 #pragma unroll
-    for (int k = 0; k < kLtChunks; ++k) {
+    for (int k = 0; k < CH; ++k) {
       float a = 0.f;
 #pragma unroll
       for (int i = 0; i < 8; ++i)
@@ -266,7 +274,7 @@ __global__ void __launch_bounds__(256, 2) lt_propose_kernel(LearnedDev d, MoveTa
     unsigned vk = 0;
     int kc = -1, klast = 0;
 #pragma unroll
-    for (int k = 0; k < kLtChunks; ++k) {
+    for (int k = 0; k < CH; ++k) {
       const bool any = __any_sync(0xffffffffu, r.valid[k] != 0u);
       if (any) klast = k;
       if (kc < 0 && any && run + csum[k] >= target) {
@@ -279,11 +287,11 @@ __global__ void __launch_bounds__(256, 2) lt_propose_kernel(LearnedDev d, MoveTa
       kc = klast;
       run = total;                         // every lane of that chunk then falls through to its last move
 #pragma unroll
-      for (int k = 0; k < kLtChunks; ++k)
+      for (int k = 0; k < CH; ++k)
         if (k == klast) run -= csum[k];
     }
 #pragma unroll
-    for (int k = 0; k < kLtChunks; ++k)
+    for (int k = 0; k < CH; ++k)
       if (k == kc) { pk = part[k]; wk = r.w[k]; vk = r.valid[k]; }
     // lanes of the chunk: inclusive scan of their sums
     float incl = pk;
@@ -328,7 +336,8 @@ __global__ void __launch_bounds__(256, 2) lt_propose_kernel(LearnedDev d, MoveTa
 }
 
 // Metropolis-Hastings acceptance with the proposed states' logits Zp (bf16).
-__global__ void __launch_bounds__(256, 2) lt_accept_kernel(LearnedDev d, MoveTable mt, unsigned t,
+template <int CH>
+__global__ void __launch_bounds__(256, CH <= 4 ? 4 : 2) lt_accept_kernel(LearnedDev d, MoveTable mt, unsigned t,
                                                         const unsigned char* prop_slots,
                                                         const __nv_bfloat16* Zp) {
   __shared__ MoveMaps mm;
@@ -344,7 +353,7 @@ __global__ void __launch_bounds__(256, 2) lt_accept_kernel(LearnedDev d, MoveTab
       prefetch_l2(prop_slots + (size_t)cn * d.n, (size_t)d.n, lane);
     }
     const __nv_bfloat16* zp = Zp + (size_t)c * d.NMp;
-    LogitRow r;
+    LogitRow<CH> r;
     load_row(zp, NM, lane, r);
     const int ladder = c / d.M, rg = d.rung[c];
     load_state(prop_slots + (size_t)c * d.n, d.n, d.delta, s_slot[w], nullptr, lane);
@@ -360,7 +369,7 @@ __global__ void __launch_bounds__(256, 2) lt_accept_kernel(LearnedDev d, MoveTab
       for (int i = lane; i < d.n; i += 32) d.slots[(size_t)c * d.n + i] = s_slot[w][i + 1];
       __nv_bfloat16* zc = d.Zcur + (size_t)c * d.NMp;
 #pragma unroll
-      for (int k = 0; k < kLtChunks; ++k)
+      for (int k = 0; k < CH; ++k)
         if (k * 256 + lane * 8 < NM) *(uint4*)(zc + k * 256 + lane * 8) = r.w[k];
       if (lane == 0) {
         d.lse[c] = lse_p;
@@ -411,6 +420,24 @@ __global__ void lt_reduce_kernel(const unsigned* in, int L, int per, unsigned lo
 }  // namespace sk
 
 namespace sk {
+
+// The per-chain kernels for the chunk count of the move table.
+#define SK_LT_CHUNKS(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
+static_assert(kLtChunks == 10, "one case per chunk count");
+struct LtKernels {
+  void (*keep)(LearnedDev, MoveTable, const __nv_bfloat16*);
+  void (*propose)(LearnedDev, MoveTable, unsigned, int, unsigned char*);
+  void (*accept)(LearnedDev, MoveTable, unsigned, const unsigned char*, const __nv_bfloat16*);
+};
+static bool lt_kernels(int ch, LtKernels* k) {
+  switch (ch) {
+#define SK_LT_CASE(c) \
+  case c: *k = {lt_keep_kernel<c>, lt_propose_kernel<c>, lt_accept_kernel<c>}; return true;
+    SK_LT_CHUNKS(SK_LT_CASE)
+#undef SK_LT_CASE
+    default: return false;
+  }
+}
 
 int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_t iters,
                    uint64_t burnin, uint64_t seed, const void* model, uint64_t* hist,
@@ -479,6 +506,12 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
   d.tswap = (const unsigned long long*)(p + o_ts);
   unsigned long long* out = (unsigned long long*)(p + o_out);
   const MoveTable mt = move_table(*m);
+  LtKernels lk;
+  if (!lt_kernels((mt.NM + 255) / 256, &lk)) {
+    cudaFree(p);
+    if (own) cudaStreamDestroy(s);
+    return SK_EINVAL;
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   e = cudaMemsetAsync(p + o_h, 0, o_b - o_h, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p + o_b, beta, (size_t)M * 8, cudaMemcpyHostToDevice, s);
@@ -494,15 +527,14 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
   const __nv_bfloat16* Zb = (const __nv_bfloat16*)m->Z;      // the forward's bf16 logits
   if (e == cudaSuccess) e = mlp_forward_dev(*m, Bp, s, true);
   if (e == cudaSuccess) {
-    lt_keep_kernel<<<chain_grid, 256, 0, s>>>(d, mt, Zb);
+    lk.keep<<<chain_grid, 256, 0, s>>>(d, mt, Zb);
     e = cudaGetLastError();
   }
   for (uint64_t t = 0; t < iters && e == cudaSuccess; ++t) {
-    lt_propose_kernel<<<chain_grid, 256, 0, s>>>(d, mt, (unsigned)t, t >= burnin ? 1 : 0,
-                                                  m->slots);
+    lk.propose<<<chain_grid, 256, 0, s>>>(d, mt, (unsigned)t, t >= burnin ? 1 : 0, m->slots);
     e = mlp_forward_dev(*m, Bp, s, true);
     if (e != cudaSuccess) break;
-    lt_accept_kernel<<<chain_grid, 256, 0, s>>>(d, mt, (unsigned)t, m->slots, Zb);
+    lk.accept<<<chain_grid, 256, 0, s>>>(d, mt, (unsigned)t, m->slots, Zb);
     lt_exchange_kernel<<<(L + 3) / 4, 128, 0, s>>>(d, (unsigned)t);
     e = cudaGetLastError();
   }

@@ -60,6 +60,40 @@ def test_trajectory_equals_oracle_at_full_size(variant, n, iters, M):
     assert np.array_equal(got["final_slots"], want["final_slots"])
 
 
+@pytest.mark.parametrize("variant,n,M,L,iters,burnin,seed", [
+    (0, 5, 6, 3, 2000, 200, 31),
+    (1, 7, 1, 2, 300, 0, 32),              # one rung: no trips
+    (0, 6, 7, 3, 70000, 35000, 33),        # across the histogram flush
+    (1, 9, 40, 5, 3001, 300, 34),          # two warps a ladder
+    (0, 12, 64, 2, 4000, 0, 35),
+    (0, 8, 16, 200, 2000, 100, 36),        # many ladders
+])
+def test_round_trips_equal_oracle(variant, n, M, L, iters, burnin, seed):
+    beta = list(np.linspace(0.0, 6.0, M) ** 1.2)
+    got = sk.pt_run(variant, n, beta, L, iters, burnin, seed, want_final=True, want_trips=True)
+    want = oracle.pt_run(variant, n, beta, L, iters, burnin, seed, want_final=True, want_trips=True)
+    assert got["round_trips"] == want["round_trips"]
+    if M >= 4:
+        assert want["round_trips"] > 0
+    # counting trips leaves the trajectory alone
+    plain = sk.pt_run(variant, n, beta, L, iters, burnin, seed, want_final=True)
+    for key in ("hist", "acc_move", "acc_swap", "final_slots"):
+        assert np.array_equal(got[key], want[key]), key
+        assert np.array_equal(got[key], plain[key]), key
+
+
+def test_round_trips_at_full_size():
+    # 64 rungs x 4096 ladders at S(64), and the report of pt_estimate_ex
+    beta = list(np.linspace(0.0, 32.0, 64))
+    got = sk.pt_run(0, 64, beta, 4096, 40, 4, 7, want_trips=True)
+    want = oracle.pt_run(0, 64, beta, 4096, 40, 4, 7, want_trips=True)
+    assert got["round_trips"] == want["round_trips"]
+    est, rep = sk.pt_estimate(0, 8, 4000, ladders=256, seed=3, beta=beta[:16], round_trips=True)
+    res = sk.pt_run(0, 8, beta[:16], 256, 4000, 400, 3, want_trips=True)
+    assert rep["round_trips"] == res["round_trips"] > 0
+    assert sk.pt_estimate(0, 8, 4000, ladders=256, seed=3, beta=beta[:16])[1]["round_trips"] == 0
+
+
 @pytest.mark.parametrize("variant,n", [(0, 4), (0, 5), (1, 4)])
 def test_ratios_against_exact_partition_function(variant, n):
     beta = np.array([0.0, 0.5, 1.0, 1.6, 2.4, 3.5, 5.0, 8.0])
