@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ __align__(8) unsigned long long full_bar[kTcStages], empty_bar[kTcStages];
   __shared__ __align__(8) unsigned long long b_bar, accf_bar[2], acce_bar[2];
   __shared__ unsigned tmem_base_s;
-  __shared__ float sbias[kTcBN];
+  __shared__ __align__(8) float sbias[kTcBN];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* base = (unsigned char*)(((size_t)tc_smem + 1023) & ~(size_t)1023);
   const int KS = g.ksplit > 1 ? g.ksplit : 1;
@@ -332,24 +332,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;");
         unsigned w[32];                              // this row's 128 bytes of the slab
+        // bf16 results two at a time: one packed round-to-nearest-even
+        // conversion per pair (element i in the low half), the bias read as
+        // float2
 #pragma unroll
-        for (int i = 0; i < kCols; ++i) {
+        for (int i = 0; i < kCols; i += 2) {
           if constexpr (EPI == kTcEpiMaskBf16) {
             const unsigned word = (&ax[i / 8].x)[(i / 2) & 3];
-            const short h = (short)((i & 1) ? (word >> 16) : (word & 0xFFFFu));
-            const float f = h > 0 ? __uint_as_float(v[i]) : 0.f;    // aux > 0 (bf16 bits)
-            const unsigned b16 = __bfloat16_as_ushort(__float2bfloat16_rn(f));
-            if (i & 1) w[i / 2] |= b16 << 16;
-            else       w[i / 2] = b16;
+            const short h0 = (short)(word & 0xFFFFu), h1 = (short)(word >> 16);
+            const float f0 = h0 > 0 ? __uint_as_float(v[i]) : 0.f;      // aux > 0 (bf16 bits)
+            const float f1 = h1 > 0 ? __uint_as_float(v[i + 1]) : 0.f;
+            const __nv_bfloat162 p = __floats2bfloat162_rn(f0, f1);
+            w[i / 2] = *(const unsigned*)&p;
           } else if constexpr (BF16) {
-            float f = __uint_as_float(v[i]) + sbias[c0 + i];
-            if constexpr (EPI == kTcEpiReluBf16) f = fmaxf(f, 0.f);
-            const unsigned b16 = __bfloat16_as_ushort(__float2bfloat16_rn(f));
-            if (i & 1) w[i / 2] |= b16 << 16;
-            else       w[i / 2] = b16;
+            const float2 bb = *(const float2*)&sbias[c0 + i];
+            float f0 = __uint_as_float(v[i]) + bb.x, f1 = __uint_as_float(v[i + 1]) + bb.y;
+            if constexpr (EPI == kTcEpiReluBf16) {
+              f0 = fmaxf(f0, 0.f);
+              f1 = fmaxf(f1, 0.f);
+            }
+            const __nv_bfloat162 p = __floats2bfloat162_rn(f0, f1);
+            w[i / 2] = *(const unsigned*)&p;
           } else {
-            const float f = __uint_as_float(v[i]) + sbias[c0 + i];
-            w[i] = __float_as_uint(f);
+            const float2 bb = *(const float2*)&sbias[c0 + i];
+            w[i] = __float_as_uint(__uint_as_float(v[i]) + bb.x);
+            w[i + 1] = __float_as_uint(__uint_as_float(v[i + 1]) + bb.y);
           }
         }
         // row `lane` of the slab, 16-byte chunk c at chunk position c ^ (row & 7)

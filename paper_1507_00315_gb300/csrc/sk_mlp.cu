@@ -372,8 +372,9 @@ cudaError_t gemm_tc(const TcGemmArgs& g, const CUtensorMap& amap, const CUtensor
 
 // Forward pass for B (multiple of 128) states whose slots are already in
 // m.slots: X, H1, H2 (bf16) and Z (fp32 logits, or bf16 with logits_bf16).
-cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s, bool logits_bf16) {
-  mlp_inputs_kernel<<<(B + 7) / 8, 256, 0, s>>>(m.slots, B, m.n, m.delta, m.K1, m.X);
+cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s, bool logits_bf16, bool inputs_ready) {
+  if (!inputs_ready)
+    mlp_inputs_kernel<<<(B + 7) / 8, 256, 0, s>>>(m.slots, B, m.n, m.delta, m.K1, m.X);
   if (m.use_tc) {
     cudaError_t e = cudaSuccess;
     if (m.wt_dirty) e = refresh_transposed(m, s);

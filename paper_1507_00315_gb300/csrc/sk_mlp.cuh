@@ -84,8 +84,10 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // Forward pass for B (multiple of 128) states whose start slots are in
 // m.slots: X, H1, H2 (bf16) and the logits Z (fp32, [B][NMp]; with
-// logits_bf16, bf16 [B][NMp] in the first half of Z's memory).
-cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s, bool logits_bf16 = false);
+// logits_bf16, bf16 [B][NMp] in the first half of Z's memory).  With
+// inputs_ready the caller has already written the input rows X.
+cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s, bool logits_bf16 = false,
+                            bool inputs_ready = false);
 MoveTable move_table(const Mlp& m);
 
 }  // namespace sk

@@ -24,14 +24,15 @@ namespace sk {
 struct LearnedDev {
   int n, delta, M, L, B, nb, NMp;
   unsigned key0, key1;
+  unsigned rk[20];           // Philox round keys of (key0, key1), computed on the host
   unsigned char* slots;      // [B][n] current configurations, c = ladder * M + l
   int* E;                    // [B]
   int* rung;                 // [B]
   int* lor;                  // [L][M]: configuration holding rung j
   __nv_bfloat16* Zcur;       // [B][NMp] logits of the current states (bf16)
   float* lse;                // [B] log-normaliser over their valid moves
-  int4* prop;                // [B] (k, old slot, new slot, dE)
-  float* lq_fwd;             // [B] log q(C' | C)
+  int4* prop;                // [B] (k | old slot << 8 | new slot << 16, dE, log q(C' | C)
+                             //      as float bits, the acceptance test's uniform word)
   unsigned* hist;            // [L][M][nb]
   unsigned* accm;            // [L][M]
   unsigned* accs;            // [L][M]
@@ -40,18 +41,20 @@ struct LearnedDev {
 };
 
 // Per-block tables of the move layout: the pair k and the start slot of
-// every move m (moves of pair k are off[k] .. off[k+1]-1), so a lane tests
-// "m is a valid move" (its slot is not the pair's current one) from the
-// tables and the state's slots in shared memory.
+// every move m (moves of pair k are off[k] .. off[k+1]-1), read for the one
+// move a chain draws; and the offsets off[k] themselves.
 constexpr int kMaxMoves = 2560;        // sum_k (2n - d_k) for n <= kMlpMaxN, padded to 256
 struct MoveMaps {
   __align__(16) unsigned char k[kMaxMoves];
   __align__(16) unsigned char s[kMaxMoves];
+  int off[kPtMaxN + 2];
 };
 
-__device__ __forceinline__ void build_move_maps(const MoveTable& mt, MoveMaps& mm) {
-  for (int m = threadIdx.x; m < kMaxMoves; m += blockDim.x) {
-    if (m >= mt.NM) {                      // padding: pair 0, never valid (slot 0 of pair 0 = 0)
+// The first `moves` entries of the tables (the chunks a kernel covers).
+__device__ __forceinline__ void build_move_maps(const MoveTable& mt, MoveMaps& mm, int moves) {
+  for (int k = threadIdx.x; k <= mt.n + 1; k += blockDim.x) mm.off[k] = k ? mt.off[k] : 0;
+  for (int m = threadIdx.x; m < moves; m += blockDim.x) {
+    if (m >= mt.NM) {                      // padding
       mm.k[m] = 0;
       mm.s[m] = 0;
       continue;
@@ -67,33 +70,35 @@ __device__ __forceinline__ void build_move_maps(const MoveTable& mt, MoveMaps& m
   }
 }
 
-// One warp loads a configuration: lane k-1 takes pair k (slot, and its two
-// bins into the occupancy counts when occ is given).  s_slot[0] = 0 makes
-// the padding moves (pair 0, slot 0) invalid.
-__device__ __forceinline__ void load_state(const unsigned char* sl, int n, int delta,
-                                           unsigned char* s_slot, int* occ, int lane) {
-  if (occ)
-    for (int i = lane; i < 2 * n; i += 32) occ[i] = 0;
-  if (lane == 0) s_slot[0] = 0;
-  __syncwarp();
-  for (int k = 1 + lane; k <= n; k += 32) {
-    const int s = sl[k - 1];
-    s_slot[k] = (unsigned char)s;
-    if (occ) {
-      atomicAdd(&occ[s], 1);
-      atomicAdd(&occ[s + k + delta], 1);
-    }
-  }
-  __syncwarp();
+// A configuration in registers: lane k-1 holds the start slot of pair k,
+// lane k-33 that of pair k > 32 (-1: no such pair).
+__device__ __forceinline__ void load_slots(const unsigned char* sl, int n, int lane, int& sa,
+                                           int& sb) {
+  sa = lane < n ? (int)sl[lane] : -1;
+  sb = lane + 32 < n ? (int)sl[lane + 32] : -1;
 }
 
-// Pull `bytes` bytes at p into L2 (one 128-byte line a lane at a time): a
-// warp asks for the next chain's rows before it works on the current one,
-// so the per-chain loads wait on L2 rather than on HBM.
-__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes, int lane) {
-  const char* c = (const char*)p;
-  for (size_t o = (size_t)lane * 128; o < bytes; o += 32 * 128)
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(c + o));
+// The start slot of pair k (1..n) from the lanes that hold the configuration.
+__device__ __forceinline__ int slot_of(int sa, int sb, int k) {
+  const int a = __shfl_sync(0xffffffffu, sa, (k - 1) & 31);
+  const int b = __shfl_sync(0xffffffffu, sb, (k - 33) & 31);
+  return k <= 32 ? a : b;
+}
+
+// Bin occupancies of the configuration into the warp's counts occ[2n].
+__device__ __forceinline__ void place_occupancy(int sa, int sb, int n, int delta, int* occ,
+                                                int lane) {
+  for (int i = lane; i < 2 * n; i += 32) occ[i] = 0;
+  __syncwarp();
+  if (sa >= 0) {
+    atomicAdd(&occ[sa], 1);
+    atomicAdd(&occ[sa + lane + 1 + delta], 1);
+  }
+  if (sb >= 0) {
+    atomicAdd(&occ[sb], 1);
+    atomicAdd(&occ[sb + lane + 33 + delta], 1);
+  }
+  __syncwarp();
 }
 
 // A chain's logit row (bf16) held in registers: chunk c of 256 moves, lane l
@@ -115,6 +120,15 @@ __device__ __forceinline__ float row_elem(const uint4& w, int i) {
   return (i & 1) ? bf16_hi(x) : bf16_lo(x);
 }
 
+// e^(z - lse) as 2^(z log2(e) - lse log2(e)): one fused multiply-add and the
+// hardware base-2 exponential (lse2 = lse log2(e)).
+__device__ __forceinline__ float exp_shifted(float z, float lse2) {
+  const float x = fmaf(z, 1.4426950408889634f, -lse2);
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 template <int CH>
 __device__ __forceinline__ void load_row(const __nv_bfloat16* z, int NM, int lane, LogitRow<CH>& r) {
 #pragma unroll
@@ -124,56 +138,64 @@ __device__ __forceinline__ void load_row(const __nv_bfloat16* z, int NM, int lan
   }
 }
 
-// Valid-move bits of the state in s_slot for the row's layout.
+// Valid-move bits of the configuration (sa, sb) for the row's layout.  A
+// state has exactly one invalid move per pair (its current slot), so the
+// lanes set those n bits in the warp's bitmask bits[CH * 8] (one atomicOr a
+// pair) and each lane reads back the byte of its 8 moves per chunk; moves
+// from NM on are invalid too.
 template <int CH>
-__device__ __forceinline__ void row_valid(const MoveMaps& mm, const unsigned char* s_slot, int NM,
-                                          int lane, LogitRow<CH>& r) {
+__device__ __forceinline__ void row_valid(const MoveMaps& mm, int sa, int sb, int NM, int lane,
+                                          unsigned* bits, LogitRow<CH>& r) {
+  for (int i = lane; i < CH * 8; i += 32) bits[i] = 0;
+  __syncwarp();
+  if (sa >= 0) {
+    const int m = mm.off[lane + 1] + sa;
+    atomicOr(&bits[m >> 5], 1u << (m & 31));
+  }
+  if (sb >= 0) {
+    const int m = mm.off[lane + 33] + sb;
+    atomicOr(&bits[m >> 5], 1u << (m & 31));
+  }
+  __syncwarp();
+  const unsigned char* by = (const unsigned char*)bits;   // byte 32 c + l: moves 256 c + 8 l ..
 #pragma unroll
   for (int c = 0; c < CH; ++c) {
     const int m0 = c * 256 + lane * 8;
-    unsigned bits = 0;
-    if (m0 < NM) {
-      const uint2 kk = *(const uint2*)&mm.k[m0];
-      const uint2 ss = *(const uint2*)&mm.s[m0];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const unsigned k = ((i < 4 ? kk.x : kk.y) >> (8 * (i & 3))) & 0xFFu;
-        const unsigned sl = ((i < 4 ? ss.x : ss.y) >> (8 * (i & 3))) & 0xFFu;
-        bits |= (unsigned)(sl != s_slot[k]) << i;
-      }
-    }
-    r.valid[c] = bits;
+    const int left = NM - m0;
+    const unsigned in = left <= 0 ? 0u : (left >= 8 ? 0xFFu : (1u << left) - 1u);
+    r.valid[c] = ~(unsigned)by[c * 32 + lane] & in;
   }
 }
 
-// log sum exp of the row over its valid moves, in one pass over the
-// registers: each lane keeps a running maximum and the sum scaled to it
-// (rescaled when the maximum grows), then the lanes' pairs are combined.
+// log sum exp of the row over its valid moves, from the registers: the
+// maximum on the packed bf16 pairs (invalid moves replaced by -inf; a bf16
+// maximum is exact), then the sum of e^(z - max) over the valid moves, each
+// reduced over the warp.
 template <int CH>
 __device__ __forceinline__ float row_lse(const LogitRow<CH>& r) {
-  float mx = -INFINITY, sum = 0.f;
+  __nv_bfloat162 acc = __halves2bfloat162(__ushort_as_bfloat16((unsigned short)0xFF80u),
+                                          __ushort_as_bfloat16((unsigned short)0xFF80u));
 #pragma unroll
   for (int c = 0; c < CH; ++c)
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
-      if ((r.valid[c] >> i) & 1u) {
-        const float z = row_elem(r.w[c], i);
-        if (z > mx) {
-          sum = sum * __expf(mx - z) + 1.f;
-          mx = z;
-        } else {
-          sum += __expf(z - mx);
-        }
-      }
+    for (int j = 0; j < 4; ++j) {
+      const unsigned x = j == 0 ? r.w[c].x : (j == 1 ? r.w[c].y : (j == 2 ? r.w[c].z : r.w[c].w));
+      const unsigned b = (r.valid[c] >> (2 * j)) & 3u;
+      const unsigned m = ((b & 1u) * 0xFFFFu) | ((b >> 1) * 0xFFFF0000u);
+      const unsigned v = (x & m) | (0xFF80FF80u & ~m);
+      acc = __hmax2(acc, *(const __nv_bfloat162*)&v);
+    }
+  const float mx = warp_max(fmaxf(__bfloat162float(acc.x), __bfloat162float(acc.y)));
+  const float mx2 = mx * 1.4426950408889634f;
+  float sum = 0.f;
 #pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    const float m2 = __shfl_xor_sync(0xffffffffu, mx, o);
-    const float s2 = __shfl_xor_sync(0xffffffffu, sum, o);
-    const float mn = fmaxf(mx, m2);
-    sum = mn == -INFINITY ? 0.f : sum * __expf(mx - mn) + s2 * __expf(m2 - mn);
-    mx = mn;
-  }
-  return mx + __logf(sum);
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float e = exp_shifted(row_elem(r.w[c], i), mx2);
+      sum += ((r.valid[c] >> i) & 1u) ? e : 0.f;
+    }
+  return mx + __logf(warp_sum(sum));
 }
 
 __global__ void lt_init_kernel(LearnedDev d) {
@@ -201,17 +223,18 @@ __global__ void lt_init_kernel(LearnedDev d) {
 // After a forward pass of the current states: keep their logits and lse.
 template <int CH>
 __global__ void __launch_bounds__(256, CH <= 4 ? 4 : 2) lt_keep_kernel(LearnedDev d, MoveTable mt,
-                                                      const __nv_bfloat16* Z) {
+                                                                      const __nv_bfloat16* Z) {
   __shared__ MoveMaps mm;
-  __shared__ unsigned char s_slot[8][kPtMaxN + 8];
-  build_move_maps(mt, mm);
+  __shared__ unsigned s_bits[8][kLtChunks * 8];
+  build_move_maps(mt, mm, 0);
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int c = blockIdx.x * 8 + w; c < d.B; c += gridDim.x * 8) {
-    load_state(d.slots + (size_t)c * d.n, d.n, d.delta, s_slot[w], nullptr, lane);
+    int sa, sb;
+    load_slots(d.slots + (size_t)c * d.n, d.n, lane, sa, sb);
     LogitRow<CH> r;
     load_row(Z + (size_t)c * d.NMp, mt.NM, lane, r);
-    row_valid(mm, s_slot[w], mt.NM, lane, r);
+    row_valid(mm, sa, sb, mt.NM, lane, s_bits[w], r);
     const float l = row_lse(r);
     __nv_bfloat16* zc = d.Zcur + (size_t)c * d.NMp;
 #pragma unroll
@@ -222,46 +245,73 @@ __global__ void __launch_bounds__(256, CH <= 4 ? 4 : 2) lt_keep_kernel(LearnedDe
   }
 }
 
-// Statistics of iteration t, then a move drawn from the current softmax; the
-// proposed configuration goes to `prop_slots` (the network's input).  The
-// draw is an inverse CDF over the valid moves in move order, from the row in
-// registers: the chunk sums (warp reductions), the chunk that holds u *
-// total, a scan of its lanes' sums, then the lane that holds it walks its 8
-// moves.
+// A chain's inputs to the propose kernel, loaded one chain ahead: its logit
+// row, its configuration (lanes), rung, energy and log-normaliser.
 template <int CH>
-__global__ void __launch_bounds__(256, CH <= 4 ? 4 : 2) lt_propose_kernel(LearnedDev d, MoveTable mt, unsigned t,
-                                                         int count_stats,
-                                                         unsigned char* prop_slots) {
+struct ProposeIn {
+  LogitRow<CH> r;
+  int sa, sb, rung, E;
+  float lse;
+};
+
+template <int CH>
+__device__ __forceinline__ void load_propose_in(const LearnedDev& d, int NM, int c, int lane,
+                                                ProposeIn<CH>& in) {
+  load_row(d.Zcur + (size_t)c * d.NMp, NM, lane, in.r);
+  load_slots(d.slots + (size_t)c * d.n, d.n, lane, in.sa, in.sb);
+  in.rung = d.rung[c];
+  in.E = d.E[c];
+  in.lse = d.lse[c];
+}
+
+// Statistics of iteration t, then a move drawn from the current softmax; the
+// proposed configuration goes to `prop_slots`, and its bin occupancies
+// straight into the network's input rows X ([B][K1] bf16), so the forward
+// that follows needs no input kernel.  The draw is an inverse CDF over the
+// valid moves in move order, from the row in registers: the chunk sums
+// (warp reductions), the chunk that holds u * total, a scan of its lanes'
+// sums, then the lane that holds it walks its 8 moves.  The proposal record
+// carries the move, dE, log q(C' | C) and the uniform word of the
+// acceptance test (the same Philox block, word 1), so the accept kernel
+// computes no Philox block of its own.  Each warp loads the next chain's row
+// and state while it works on the current one.
+template <int CH>
+__global__ void __launch_bounds__(256, CH <= 4 ? 3 : 2)
+    lt_propose_kernel(LearnedDev d, MoveTable mt, unsigned t, int count_stats,
+                      unsigned char* prop_slots, __nv_bfloat16* X, int K1) {
   __shared__ MoveMaps mm;
   __shared__ int s_occ[8][2 * kPtMaxN];
-  __shared__ unsigned char s_slot[8][kPtMaxN + 8];
-  build_move_maps(mt, mm);
+  __shared__ unsigned s_bits[8][kLtChunks * 8];
+  build_move_maps(mt, mm, CH * 256);
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int NM = mt.NM;
-  for (int c = blockIdx.x * 8 + w; c < d.B; c += gridDim.x * 8) {
-    const int cn = c + gridDim.x * 8;
-    if (cn < d.B) {
-      prefetch_l2(d.Zcur + (size_t)cn * d.NMp, (size_t)NM * 2, lane);
-      prefetch_l2(d.slots + (size_t)cn * d.n, (size_t)d.n, lane);
-    }
-    LogitRow<CH> r;
-    load_row(d.Zcur + (size_t)c * d.NMp, NM, lane, r);
-    const int ladder = c / d.M, rg = d.rung[c], E = d.E[c];
-    if (lane == 0 && count_stats) d.hist[((size_t)ladder * d.M + rg) * d.nb + E] += 1;
-    load_state(d.slots + (size_t)c * d.n, d.n, d.delta, s_slot[w], s_occ[w], lane);
-    row_valid(mm, s_slot[w], NM, lane, r);
-    const float lse = d.lse[c];
-    const uint4 rw = philox4x32_10(make_uint4(t, (unsigned)rg, (unsigned)ladder, 5u), d.key0, d.key1);
+  const int NM = mt.NM, stride = gridDim.x * 8;
+  int c = blockIdx.x * 8 + w;
+  ProposeIn<CH> cur;
+  if (c < d.B) load_propose_in(d, NM, c, lane, cur);
+  for (; c < d.B; c += stride) {
+    ProposeIn<CH> nxt;
+    if (c + stride < d.B) load_propose_in(d, NM, c + stride, lane, nxt);
+    const int ladder = c / d.M, rg = cur.rung;
+    if (lane == 0 && count_stats)
+      atomicAdd(&d.hist[((size_t)ladder * d.M + rg) * d.nb + cur.E], 1u);
+    place_occupancy(cur.sa, cur.sb, d.n, d.delta, s_occ[w], lane);
+    LogitRow<CH>& r = cur.r;
+    row_valid(mm, cur.sa, cur.sb, NM, lane, s_bits[w], r);
+    const float lse = cur.lse;
+    const uint4 rw = philox4x32_10_rk(make_uint4(t, (unsigned)rg, (unsigned)ladder, 5u), d.rk);
     // per lane and chunk: the sum of exp(z - lse) over its valid moves
+    const float lse2 = lse * 1.4426950408889634f;
     float part[CH], csum[CH];
     float total = 0.f;
 #pragma unroll
     for (int k = 0; k < CH; ++k) {
       float a = 0.f;
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
-        if ((r.valid[k] >> i) & 1u) a += __expf(row_elem(r.w[k], i) - lse);
+      for (int i = 0; i < 8; ++i) {
+        const float e = exp_shifted(row_elem(r.w[k], i), lse2);
+        a += ((r.valid[k] >> i) & 1u) ? e : 0.f;
+      }
       part[k] = a;
       csum[k] = warp_sum(a);
       total += csum[k];
@@ -303,81 +353,136 @@ __global__ void __launch_bounds__(256, CH <= 4 ? 4 : 2) lt_propose_kernel(Learne
     const unsigned hit = __ballot_sync(0xffffffffu, vk != 0u && run + incl >= target);
     const unsigned withv = __ballot_sync(0xffffffffu, vk != 0u);
     const int ln = hit ? __ffs(hit) - 1 : 31 - __clz(withv);   // withv != 0: the chunk has valid moves
-    int pick_i = -1;
-    if (lane == ln) {
-      float a = run + incl - pk;           // exclusive: the running sum before this lane's moves
-      int last = -1;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        if ((vk >> i) & 1u) {
-          last = i;
-          a += __expf(row_elem(wk, i) - lse);
-          if (pick_i < 0 && a >= target) pick_i = i;
-        }
-      }
-      if (pick_i < 0) pick_i = last;
-    }
-    pick_i = __shfl_sync(0xffffffffu, pick_i, ln);
+    // that lane's 8 moves, one a lane on lanes 0..7: the running sum before
+    // them, a scan of their terms, the first that reaches the target (else
+    // its last valid move)
+    const float excl = __shfl_sync(0xffffffffu, run + incl - pk, ln);
+    const unsigned vl = __shfl_sync(0xffffffffu, vk, ln);
     const uint4 wp = make_uint4(__shfl_sync(0xffffffffu, wk.x, ln), __shfl_sync(0xffffffffu, wk.y, ln),
                                 __shfl_sync(0xffffffffu, wk.z, ln), __shfl_sync(0xffffffffu, wk.w, ln));
+    const int li = lane & 7;
+    const bool vi = lane < 8 && ((vl >> li) & 1u);
+    float sc = vi ? exp_shifted(row_elem(wp, li), lse2) : 0.f;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const float u = __shfl_up_sync(0xffffffffu, sc, o, 8);
+      if (li >= o) sc += u;
+    }
+    const unsigned hit8 = __ballot_sync(0xffffffffu, vi && excl + sc >= target);
+    const unsigned val8 = __ballot_sync(0xffffffffu, vi);
+    const int pick_i = hit8 ? __ffs(hit8) - 1 : 31 - __clz(val8);
     const int pick = kc * 256 + ln * 8 + pick_i;
     const int kp = mm.k[pick];
-    const int s_new = mm.s[pick], s_old = s_slot[w][kp];
-    const int dE = move_delta_e(s_occ[w], s_old, kp + d.delta, s_new);
+    const int s_new = mm.s[pick], s_old = slot_of(cur.sa, cur.sb, kp);
+    const int dk = kp + d.delta;
+    const int dE = move_delta_e(s_occ[w], s_old, dk, s_new);
     unsigned char* ps = prop_slots + (size_t)c * d.n;
-    for (int i = lane; i < d.n; i += 32)
-      ps[i] = (i + 1 == kp) ? (unsigned char)s_new : s_slot[w][i + 1];
+    if (cur.sa >= 0) ps[lane] = (unsigned char)(lane + 1 == kp ? s_new : cur.sa);
+    if (cur.sb >= 0) ps[lane + 32] = (unsigned char)(lane + 33 == kp ? s_new : cur.sb);
     if (lane == 0) {
-      d.prop[c] = make_int4(kp, s_old, s_new, dE);
-      d.lq_fwd[c] = row_elem(wp, pick_i) - lse;
+      d.prop[c] = make_int4(kp | (s_old << 8) | (s_new << 16), dE,
+                            __float_as_int(row_elem(wp, pick_i) - lse), (int)rw.y);
+      // the proposed configuration's occupancies
+      s_occ[w][s_old] -= 1;
+      s_occ[w][s_old + dk] -= 1;
+      s_occ[w][s_new] += 1;
+      s_occ[w][s_new + dk] += 1;
     }
     __syncwarp();
+    // its network input row: four adjacent bf16 occupancies a lane (one
+    // 8-byte store; bins beyond 2n are 0)
+    for (int col = lane * 4; col < K1; col += 128) {
+      unsigned short h[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        h[i] = __bfloat16_as_ushort(
+            __float2bfloat16(col + i < 2 * d.n ? (float)s_occ[w][col + i] : 0.f));
+      *(uint2*)(X + (size_t)c * K1 + col) =
+          make_uint2((unsigned)h[0] | ((unsigned)h[1] << 16), (unsigned)h[2] | ((unsigned)h[3] << 16));
+    }
+    __syncwarp();
+    cur = nxt;
   }
 }
 
-// Metropolis-Hastings acceptance with the proposed states' logits Zp (bf16).
+// A chain's inputs to the accept kernel, loaded one chain ahead: the
+// proposed state's logit row and configuration, the rung and the proposal
+// record.
 template <int CH>
-__global__ void __launch_bounds__(256, CH <= 4 ? 4 : 2) lt_accept_kernel(LearnedDev d, MoveTable mt, unsigned t,
-                                                        const unsigned char* prop_slots,
-                                                        const __nv_bfloat16* Zp) {
+struct AcceptIn {
+  LogitRow<CH> r;
+  int sa, sb, rung;
+  int4 pr;
+};
+
+template <int CH>
+__device__ __forceinline__ void load_accept_in(const LearnedDev& d, const __nv_bfloat16* Zp,
+                                               const unsigned char* prop_slots, int NM, int c,
+                                               int lane, AcceptIn<CH>& in) {
+  load_row(Zp + (size_t)c * d.NMp, NM, lane, in.r);
+  load_slots(prop_slots + (size_t)c * d.n, d.n, lane, in.sa, in.sb);
+  in.rung = d.rung[c];
+  in.pr = d.prop[c];
+}
+
+// Metropolis-Hastings acceptance with the proposed states' logits Zp (bf16):
+// the log-normaliser of the proposed row and its logit of the reverse move
+// (taken from the lane that holds it), then the decision with the uniform
+// word the propose kernel drew; an accepted state keeps its row as the
+// chain's current logits.  Each warp loads the next chain's inputs while it
+// works on the current one.
+template <int CH>
+__global__ void __launch_bounds__(256, CH <= 4 ? 3 : 2)
+    lt_accept_kernel(LearnedDev d, MoveTable mt, unsigned t, const unsigned char* prop_slots,
+                     const __nv_bfloat16* Zp) {
   __shared__ MoveMaps mm;
-  __shared__ unsigned char s_slot[8][kPtMaxN + 8];
-  build_move_maps(mt, mm);
+  __shared__ unsigned s_bits[8][kLtChunks * 8];
+  __shared__ double s_beta[kPtMaxRungsLearned];
+  build_move_maps(mt, mm, 0);
+  for (int i = threadIdx.x; i < d.M; i += blockDim.x) s_beta[i] = d.beta[i];
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int NM = mt.NM;
-  for (int c = blockIdx.x * 8 + w; c < d.B; c += gridDim.x * 8) {
-    const int cn = c + gridDim.x * 8;
-    if (cn < d.B) {
-      prefetch_l2(Zp + (size_t)cn * d.NMp, (size_t)NM * 2, lane);
-      prefetch_l2(prop_slots + (size_t)cn * d.n, (size_t)d.n, lane);
-    }
-    const __nv_bfloat16* zp = Zp + (size_t)c * d.NMp;
-    LogitRow<CH> r;
-    load_row(zp, NM, lane, r);
-    const int ladder = c / d.M, rg = d.rung[c];
-    load_state(prop_slots + (size_t)c * d.n, d.n, d.delta, s_slot[w], nullptr, lane);
-    row_valid(mm, s_slot[w], NM, lane, r);
+  const int NM = mt.NM, stride = gridDim.x * 8;
+  int c = blockIdx.x * 8 + w;
+  AcceptIn<CH> cur;
+  if (c < d.B) load_accept_in(d, Zp, prop_slots, NM, c, lane, cur);
+  for (; c < d.B; c += stride) {
+    AcceptIn<CH> nxt;
+    if (c + stride < d.B) load_accept_in(d, Zp, prop_slots, NM, c + stride, lane, nxt);
+    const int ladder = c / d.M, rg = cur.rung;
+    LogitRow<CH>& r = cur.r;
+    row_valid(mm, cur.sa, cur.sb, NM, lane, s_bits[w], r);
     const float lse_p = row_lse(r);
-    const int4 pr = d.prop[c];
-    const float lq_rev = __bfloat162float(zp[mt.off[pr.x] + pr.y]) - lse_p;
-    const float log_a = (float)(-d.beta[rg] * (double)pr.w) + lq_rev - d.lq_fwd[c];
-    const uint4 rw = philox4x32_10(make_uint4(t, (unsigned)rg, (unsigned)ladder, 5u), d.key0, d.key1);
-    const float u = ((float)rw.y + 0.5f) * 2.3283064365386963e-10f;
+    // the reverse move (k, old slot): chunk, lane and element that hold it
+    const int kp = cur.pr.x & 0xFF, s_old = (cur.pr.x >> 8) & 0xFF, dE = cur.pr.y;
+    const int idx = mm.off[kp] + s_old;
+    const int kc = idx >> 8, ln = (idx & 255) >> 3, ei = idx & 7;
+    uint4 wk = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int k = 0; k < CH; ++k)
+      if (k == kc) wk = r.w[k];
+    const uint4 wr = make_uint4(__shfl_sync(0xffffffffu, wk.x, ln), __shfl_sync(0xffffffffu, wk.y, ln),
+                                __shfl_sync(0xffffffffu, wk.z, ln), __shfl_sync(0xffffffffu, wk.w, ln));
+    const float lq_rev = row_elem(wr, ei) - lse_p;
+    const float log_a = (float)(-s_beta[rg] * (double)dE) + lq_rev - __int_as_float(cur.pr.z);
+    const float u = ((float)(unsigned)cur.pr.w + 0.5f) * 2.3283064365386963e-10f;
     const bool acc = log_a >= 0.f || logf(u) < log_a;
     if (acc) {
-      for (int i = lane; i < d.n; i += 32) d.slots[(size_t)c * d.n + i] = s_slot[w][i + 1];
+      unsigned char* sl = d.slots + (size_t)c * d.n;
+      if (cur.sa >= 0) sl[lane] = (unsigned char)cur.sa;
+      if (cur.sb >= 0) sl[lane + 32] = (unsigned char)cur.sb;
       __nv_bfloat16* zc = d.Zcur + (size_t)c * d.NMp;
 #pragma unroll
       for (int k = 0; k < CH; ++k)
         if (k * 256 + lane * 8 < NM) *(uint4*)(zc + k * 256 + lane * 8) = r.w[k];
       if (lane == 0) {
         d.lse[c] = lse_p;
-        d.E[c] += pr.w;
-        d.accm[(size_t)ladder * d.M + rg] += 1;
+        atomicAdd(&d.E[c], dE);
+        atomicAdd(&d.accm[(size_t)ladder * d.M + rg], 1u);
       }
     }
     __syncwarp();
+    cur = nxt;
   }
 }
 
@@ -426,7 +531,7 @@ namespace sk {
 static_assert(kLtChunks == 10, "one case per chunk count");
 struct LtKernels {
   void (*keep)(LearnedDev, MoveTable, const __nv_bfloat16*);
-  void (*propose)(LearnedDev, MoveTable, unsigned, int, unsigned char*);
+  void (*propose)(LearnedDev, MoveTable, unsigned, int, unsigned char*, __nv_bfloat16*, int);
   void (*accept)(LearnedDev, MoveTable, unsigned, const unsigned char*, const __nv_bfloat16*);
 };
 static bool lt_kernels(int ch, LtKernels* k) {
@@ -469,6 +574,10 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
   std::memset(&d, 0, sizeof(d));
   d.n = n; d.delta = m->delta; d.M = M; d.L = L; d.B = B; d.nb = nb; d.NMp = m->NMp;
   d.key0 = (unsigned)seed; d.key1 = (unsigned)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    d.rk[2 * r] = d.key0 + 0x9E3779B9u * (unsigned)r;
+    d.rk[2 * r + 1] = d.key1 + 0xBB67AE85u * (unsigned)r;
+  }
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
   size_t off = 0;
   const size_t o_sl = off; off = al(off + (size_t)B * n);
@@ -478,7 +587,6 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
   const size_t o_z = off; off = al(off + (size_t)B * m->NMp * 2);
   const size_t o_lse = off; off = al(off + (size_t)B * 4);
   const size_t o_pr = off; off = al(off + (size_t)B * 16);
-  const size_t o_lq = off; off = al(off + (size_t)B * 4);
   const size_t o_h = off; off = al(off + (size_t)L * M * nb * 4);
   const size_t o_am = off; off = al(off + (size_t)L * M * 4);
   const size_t o_as = off; off = al(off + (size_t)L * M * 4);
@@ -498,7 +606,6 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
   d.Zcur = (__nv_bfloat16*)(p + o_z);
   d.lse = (float*)(p + o_lse);
   d.prop = (int4*)(p + o_pr);
-  d.lq_fwd = (float*)(p + o_lq);
   d.hist = (unsigned*)(p + o_h);
   d.accm = (unsigned*)(p + o_am);
   d.accs = (unsigned*)(p + o_as);
@@ -531,8 +638,9 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
     e = cudaGetLastError();
   }
   for (uint64_t t = 0; t < iters && e == cudaSuccess; ++t) {
-    lk.propose<<<chain_grid, 256, 0, s>>>(d, mt, (unsigned)t, t >= burnin ? 1 : 0, m->slots);
-    e = mlp_forward_dev(*m, Bp, s, true);
+    lk.propose<<<chain_grid, 256, 0, s>>>(d, mt, (unsigned)t, t >= burnin ? 1 : 0, m->slots, m->X,
+                                          m->K1);
+    e = mlp_forward_dev(*m, Bp, s, true, true);     // propose wrote the input rows
     if (e != cudaSuccess) break;
     lk.accept<<<chain_grid, 256, 0, s>>>(d, mt, (unsigned)t, m->slots, Zb);
     lt_exchange_kernel<<<(L + 3) / 4, 128, 0, s>>>(d, (unsigned)t);
