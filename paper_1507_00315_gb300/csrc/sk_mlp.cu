@@ -115,17 +115,53 @@ namespace sk {
 
 // One warp per state: target t(m) ~ exp(-beta* dE(m)) over the valid moves,
 // q = masked softmax of the logits, dZ = (q - t) / B, loss += -sum t log q / B.
+// The state's logit row is loaded at once into registers (CH chunks of 256
+// moves, lane l holding moves 256 c + 8 l .. + 7, two 16-byte loads a chunk);
+// the pair and slot of each move come from a per-block table, dE from the
+// state's bin counts in shared memory.  One instantiation per CH = NMp / 256.
+template <int CH>
 __global__ void __launch_bounds__(256)
     mlp_loss_kernel(const float* __restrict__ Z, int ldz, const unsigned char* __restrict__ slots,
                     int B, MoveTable mt, float beta_star, float inv_B, __nv_bfloat16* dZ,
                     float* loss) {
+  __shared__ unsigned char mk[CH * 256], msl[CH * 256];
   __shared__ int s_occ[8][2 * kPtMaxN];
   __shared__ unsigned char s_slot[8][kPtMaxN + 1];
+  for (int m = threadIdx.x; m < CH * 256; m += blockDim.x) {
+    int k = 0, sl = 0;
+    if (m < mt.NM) {                       // the pair with off[k] <= m < off[k+1]
+      int lo = 1, hi = mt.n;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (mt.off[mid] <= m) lo = mid;
+        else hi = mid - 1;
+      }
+      k = lo;
+      sl = m - mt.off[lo];
+    }
+    mk[m] = (unsigned char)k;
+    msl[m] = (unsigned char)sl;
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int b = blockIdx.x * 8 + w;
   if (b >= B) return;
-  const int n = mt.n, bins = 2 * n;
-  for (int i = lane; i < bins; i += 32) s_occ[w][i] = 0;
+  const int n = mt.n, NM = mt.NM;
+  float z[CH][8];
+  const float* zr = Z + (size_t)b * ldz;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int m0 = c * 256 + lane * 8;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), e = a;
+    if (m0 < NM) {
+      a = __ldg((const float4*)(zr + m0));
+      e = __ldg((const float4*)(zr + m0 + 4));
+    }
+    z[c][0] = a.x; z[c][1] = a.y; z[c][2] = a.z; z[c][3] = a.w;
+    z[c][4] = e.x; z[c][5] = e.y; z[c][6] = e.z; z[c][7] = e.w;
+  }
+  for (int i = lane; i < 2 * n; i += 32) s_occ[w][i] = 0;
+  if (lane == 0) s_slot[w][0] = 0;
   __syncwarp();
   for (int k = 1 + lane; k <= n; k += 32) {           // lane k-1 places pair k
     const int s = slots[(size_t)b * n + (k - 1)];
@@ -134,45 +170,87 @@ __global__ void __launch_bounds__(256)
     atomicAdd(&s_occ[w][s + k + mt.delta], 1);
   }
   __syncwarp();
-  const float* z = Z + (size_t)b * ldz;
-  float zmax = -INFINITY, wmax = -INFINITY;
-  for (int m = lane, k = 1; m < mt.NM; m += 32) {
-    while (m >= mt.off[k + 1]) ++k;
-    const int s = m - mt.off[k], sk = s_slot[w][k];
-    if (s == sk) continue;
-    const int de = move_delta_e(s_occ[w], sk, k + mt.delta, s);
-    zmax = fmaxf(zmax, z[m]);
-    wmax = fmaxf(wmax, -beta_star * (float)de);
+  // valid moves and their dE
+  int de[CH][8];
+  unsigned vb[CH];
+  float zmax = -INFINITY;
+  int demin = 1 << 20;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    vb[c] = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int m = c * 256 + lane * 8 + i;
+      const int k = mk[m], sl = msl[m];
+      const int sk = s_slot[w][k];
+      const bool v = m < NM && sl != sk;     // padding: pair 0, slot 0 = s_slot[0]
+      de[c][i] = v ? move_delta_e(s_occ[w], sk, k + mt.delta, sl) : 0;
+      vb[c] |= (unsigned)v << i;
+      if (v) {
+        zmax = fmaxf(zmax, z[c][i]);
+        demin = min(demin, de[c][i]);
+      }
+    }
   }
   zmax = warp_max(zmax);
-  wmax = warp_max(wmax);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) demin = min(demin, __shfl_xor_sync(0xffffffffu, demin, o));
+  const float wmax = -beta_star * (float)demin;
   float sq = 0.f, stt = 0.f;
-  for (int m = lane, k = 1; m < mt.NM; m += 32) {
-    while (m >= mt.off[k + 1]) ++k;
-    const int s = m - mt.off[k], sk = s_slot[w][k];
-    if (s == sk) continue;
-    const int de = move_delta_e(s_occ[w], sk, k + mt.delta, s);
-    sq += __expf(z[m] - zmax);
-    stt += __expf(-beta_star * (float)de - wmax);
-  }
+#pragma unroll
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if ((vb[c] >> i) & 1u) {
+        sq += __expf(z[c][i] - zmax);
+        stt += __expf(-beta_star * (float)de[c][i] - wmax);
+      }
   sq = warp_sum(sq);
   stt = warp_sum(stt);
   const float lse = zmax + __logf(sq);
   float l = 0.f;
   __nv_bfloat16* dz = dZ + (size_t)b * ldz;
-  for (int m = lane, k = 1; m < ldz; m += 32) {
-    if (m >= mt.NM) { dz[m] = __float2bfloat16(0.f); continue; }
-    while (m >= mt.off[k + 1]) ++k;
-    const int s = m - mt.off[k], sk = s_slot[w][k];
-    if (s == sk) { dz[m] = __float2bfloat16(0.f); continue; }
-    const int de = move_delta_e(s_occ[w], sk, k + mt.delta, s);
-    const float q = __expf(z[m] - lse);
-    const float t = __expf(-beta_star * (float)de - wmax) / stt;
-    dz[m] = __float2bfloat16((q - t) * inv_B);
-    l -= t * (z[m] - lse);
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    unsigned wd[4];
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) {
+      float g[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        g[h] = 0.f;
+        if ((vb[c] >> (i + h)) & 1u) {
+          const float q = __expf(z[c][i + h] - lse);
+          const float t = __expf(-beta_star * (float)de[c][i + h] - wmax) / stt;
+          g[h] = (q - t) * inv_B;
+          l -= t * (z[c][i + h] - lse);
+        }
+      }
+      const __nv_bfloat162 p2 = __floats2bfloat162_rn(g[0], g[1]);
+      wd[i / 2] = *(const unsigned*)&p2;
+    }
+    *(uint4*)(dz + c * 256 + lane * 8) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
   }
   l = warp_sum(l);
   if (lane == 0) atomicAdd(loss, l * inv_B);
+}
+
+// The loss kernel for the model's move-table size (NMp / 256 chunks).
+static cudaError_t launch_loss(const Mlp& m, int B, float beta_star, float* loss, cudaStream_t s) {
+  const MoveTable mt = move_table(m);
+  const dim3 grid((B + 7) / 8), block(256);
+  switch (m.NMp / 256) {
+#define SK_LOSS_CASE(c)                                                                     \
+  case c:                                                                                   \
+    mlp_loss_kernel<c><<<grid, block, 0, s>>>(m.Z, m.NMp, m.slots, B, mt, beta_star,       \
+                                              1.0f / (float)B, m.dZ, loss);                 \
+    break;
+    SK_LOSS_CASE(1) SK_LOSS_CASE(2) SK_LOSS_CASE(3) SK_LOSS_CASE(4) SK_LOSS_CASE(5)
+    SK_LOSS_CASE(6) SK_LOSS_CASE(7) SK_LOSS_CASE(8) SK_LOSS_CASE(9) SK_LOSS_CASE(10)
+#undef SK_LOSS_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 MoveTable move_table(const Mlp& m) {
@@ -532,8 +610,8 @@ cudaError_t mlp_backward_dev(Mlp& m, int B, float beta_star, cudaStream_t s,
   if (!m.use_tc) e = cudaMemsetAsync(m.gW1, 0, m.nparams * sizeof(float), s);  // atomics add up
   if (e == cudaSuccess && !loss) e = cudaMemsetAsync(m.loss, 0, sizeof(float), s);
   if (e != cudaSuccess) return e;
-  mlp_loss_kernel<<<(B + 7) / 8, 256, 0, s>>>(m.Z, m.NMp, m.slots, B, move_table(m), beta_star,
-                                              1.0f / (float)B, m.dZ, loss ? loss : m.loss);
+  e = launch_loss(m, B, beta_star, loss ? loss : m.loss, s);
+  if (e != cudaSuccess) return e;
   if (m.use_tc) {
     // tcgen05: dH = (dZ W^T) * [H > 0] with W streamed as B, on s; the
     // weight and bias gradients (K-major copies, a fixed-order K split) on a
