@@ -359,12 +359,15 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // 2D tensor map of a row-major [rows][cols] matrix of bf16 (esize 2) or
 // fp32 (esize 4), box [box_rows][128 bytes], 128-byte swizzle.
+// A 2-D map of rows x cols elements, ld elements between rows (ld >= cols;
+// 0: ld = cols); boxes of 128 bytes x box_rows, 128-byte swizzle.  A TMA
+// store writes only the part of a box inside the map.
 static bool encode_map(CUtensorMap* map, const void* ptr, int esize, int rows, int cols,
-                       int box_rows) {
+                       int box_rows, int ld = 0) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)cols * esize};
+  const cuuint64_t strides[1] = {(cuuint64_t)(ld > 0 ? ld : cols) * esize};
   const cuuint32_t box[2] = {(cuuint32_t)(128 / esize), (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return enc(map, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
@@ -383,7 +386,10 @@ static bool make_tc_maps(Mlp& m) {
          encode_map(&m.tmC[0], m.H1, 2, m.max_batch, kHidden, 32) &&
          encode_map(&m.tmC[1], m.H2, 2, m.max_batch, kHidden, 32) &&
          encode_map(&m.tmC[2], m.Z, 4, m.max_batch, m.NMp, 32) &&
-         encode_map(&m.tmZb, m.Z, 2, m.max_batch, m.NMp, 32) &&
+         // the chains' bf16 logits: only the move table's columns (rounded
+         // up to 8, whole 16-byte words; those columns' weights are 0) are
+         // stored, the row stride stays NMp
+         encode_map(&m.tmZb, m.Z, 2, m.max_batch, (m.NM + 7) / 8 * 8, 32, m.NMp) &&
          encode_map(&m.tmBA[0], m.dZ, 2, m.max_batch, m.NMp, kTcBM) &&
          encode_map(&m.tmBA[1], m.dH2, 2, m.max_batch, kHidden, kTcBM) &&
          encode_map(&m.tmBB[0], m.W3, 2, kHidden, m.NMp, kTcBN) &&
@@ -459,7 +465,7 @@ cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s, bool logits_bf16, boo
     if (e != cudaSuccess) return e;
     TcGemmArgs t;
     std::memset(&t, 0, sizeof(t));
-    t.M = B; t.N = kHidden; t.K = m.K1; t.bias = m.b1; t.err = m.tc_err;
+    t.M = B; t.N = kHidden; t.K = m.K1f; t.bias = m.b1; t.err = m.tc_err;
     e = gemm_tc(t, m.tmA[0], m.tmB[0], m.tmC[0], kTcEpiReluBf16, s);
     if (e != cudaSuccess) return e;
     t.K = kHidden; t.bias = m.b2;
@@ -471,7 +477,7 @@ cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s, bool logits_bf16, boo
   }
   GemmArgs g;
   std::memset(&g, 0, sizeof(g));
-  g.M = B; g.N = kHidden; g.K = m.K1; g.A = m.X; g.lda = m.K1; g.B = m.W1; g.ldb = kHidden;
+  g.M = B; g.N = kHidden; g.K = m.K1f; g.A = m.X; g.lda = m.K1; g.B = m.W1; g.ldb = kHidden;
   g.C = m.H1; g.ldc = kHidden; g.bias = m.b1;
   cudaError_t e = gemm<false, false, EPI_BF16_RELU>(g, 1, s);
   if (e != cudaSuccess) return e;
@@ -713,6 +719,7 @@ int mlp_create(int variant, int n, int max_batch, uint64_t seed, Mlp** out) {
   m->delta = variant == SK_LANGFORD ? 1 : 0;
   m->bins = 2 * n;
   m->K1 = 128;
+  m->K1f = (2 * n + 63) / 64 * 64;
   m->max_batch = max_batch;
   m->off[1] = 0;
   for (int k = 1; k <= n; ++k) m->off[k + 1] = m->off[k] + (2 * n - (k + m->delta));

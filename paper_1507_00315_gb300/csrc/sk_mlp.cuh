@@ -16,7 +16,9 @@ constexpr int kHidden = 256;
 
 struct Mlp {
   int variant, n, delta, bins;
-  int K1;                 // input width, padded to 128
+  int K1;                 // input width, padded to 128 (the row stride of X, the rows of W1)
+  int K1f;                // the forward's input width: 2n rounded up to 64 (the columns
+                          // of X beyond 2n are 0, so the first layer's sum stops there)
   int NM, NMp;            // moves, padded to 256
   int max_batch;
   int off[kPtMaxN + 2];   // move offsets per pair k (1-based), off[n+1] = NM

@@ -6,8 +6,9 @@
 // q(C | C') is the probability of the reverse move (k, old slot) under the
 // proposed state's logits, so the chains keep the Boltzmann weights of the
 // plain ones.  Configurations live in global memory; per iteration the
-// network runs once, on every proposed state, and an accepted state keeps its
-// logits for the next draw.
+// network runs once, on every proposed state, then one kernel tests every
+// chain's move and draws its next one; an accepted state keeps its logits and
+// per-lane weight sums, so a rejected move costs no second pass over a row.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,6 +32,9 @@ struct LearnedDev {
   int* lor;                  // [L][M]: configuration holding rung j
   __nv_bfloat16* Zcur;       // [B][NMp] logits of the current states (bf16)
   float* lse;                // [B] log-normaliser over their valid moves
+  float* mx;                 // [B] the shift of their stored weight sums (the row's maximum)
+  float* parts;              // [B][CH][32] per lane and chunk: sum of e^(z - mx) over the
+                             //   lane's valid moves of the chunk (the current state's)
   int4* prop;                // [B] (k | old slot << 8 | new slot << 16, dE, log q(C' | C)
                              //      as float bits, the acceptance test's uniform word)
   unsigned* hist;            // [L][M][nb]
@@ -80,6 +84,14 @@ __device__ __forceinline__ void load_slots(const unsigned char* sl, int n, int l
 
 // The start slot of pair k (1..n) from the lanes that hold the configuration.
 __device__ __forceinline__ int slot_of(int sa, int sb, int k) {
+  const int a = __shfl_sync(0xffffffffu, sa, (k - 1) & 31);
+  const int b = __shfl_sync(0xffffffffu, sb, (k - 33) & 31);
+  return k <= 32 ? a : b;
+}
+
+// The start slot of pair k (1..n, a different pair on each lane) from the
+// lanes that hold the configuration.
+__device__ __forceinline__ int slot_of_lanes(int sa, int sb, int k) {
   const int a = __shfl_sync(0xffffffffu, sa, (k - 1) & 31);
   const int b = __shfl_sync(0xffffffffu, sb, (k - 33) & 31);
   return k <= 32 ? a : b;
@@ -167,35 +179,107 @@ __device__ __forceinline__ void row_valid(const MoveMaps& mm, int sa, int sb, in
   }
 }
 
-// log sum exp of the row over its valid moves, from the registers: the
-// maximum on the packed bf16 pairs (invalid moves replaced by -inf; a bf16
-// maximum is exact), then the sum of e^(z - max) over the valid moves, each
-// reduced over the warp.
+// The largest element of the row (valid moves or not; the words beyond the
+// table hold -inf, the padding columns inside the last word 0): a shift for
+// the weights that needs no masks.
 template <int CH>
-__device__ __forceinline__ float row_lse(const LogitRow<CH>& r) {
-  __nv_bfloat162 acc = __halves2bfloat162(__ushort_as_bfloat16((unsigned short)0xFF80u),
-                                          __ushort_as_bfloat16((unsigned short)0xFF80u));
+__device__ __forceinline__ float row_max_all(const LogitRow<CH>& r) {
+  __nv_bfloat162 acc = *(const __nv_bfloat162*)&r.w[0].x;
 #pragma unroll
-  for (int c = 0; c < CH; ++c)
+  for (int c = 0; c < CH; ++c) {
+    if (c) acc = __hmax2(acc, *(const __nv_bfloat162*)&r.w[c].x);
+    acc = __hmax2(acc, *(const __nv_bfloat162*)&r.w[c].y);
+    acc = __hmax2(acc, *(const __nv_bfloat162*)&r.w[c].z);
+    acc = __hmax2(acc, *(const __nv_bfloat162*)&r.w[c].w);
+  }
+  return warp_max(fmaxf(__bfloat162float(acc.x), __bfloat162float(acc.y)));
+}
+
+// This lane's sums, per chunk, of e^(z - shift) over its valid moves (shift2
+// = shift log2(e)); returns their total.
+template <int CH>
+__device__ __forceinline__ float row_parts(const LogitRow<CH>& r, float shift2, float* part) {
+  float tot = 0.f;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const unsigned x = j == 0 ? r.w[c].x : (j == 1 ? r.w[c].y : (j == 2 ? r.w[c].z : r.w[c].w));
-      const unsigned b = (r.valid[c] >> (2 * j)) & 3u;
-      const unsigned m = ((b & 1u) * 0xFFFFu) | ((b >> 1) * 0xFFFF0000u);
-      const unsigned v = (x & m) | (0xFF80FF80u & ~m);
-      acc = __hmax2(acc, *(const __nv_bfloat162*)&v);
-    }
-  const float mx = warp_max(fmaxf(__bfloat162float(acc.x), __bfloat162float(acc.y)));
-  const float mx2 = mx * 1.4426950408889634f;
-  float sum = 0.f;
-#pragma unroll
-  for (int c = 0; c < CH; ++c)
+  for (int c = 0; c < CH; ++c) {
+    float a = 0.f;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const float e = exp_shifted(row_elem(r.w[c], i), mx2);
-      sum += ((r.valid[c] >> i) & 1u) ? e : 0.f;
+      const float e = exp_shifted(row_elem(r.w[c], i), shift2);
+      a += ((r.valid[c] >> i) & 1u) ? e : 0.f;
     }
-  return mx + __logf(warp_sum(sum));
+    part[c] = a;
+    tot += a;
+  }
+  return tot;
+}
+
+// The inverse-CDF draw at u * total over the weights e^(z - shift) of the
+// valid moves, taken in (lane, chunk, element) order (any fixed order gives
+// the same distribution), in two parts.  draw_select: from this lane's
+// per-chunk sums, an inclusive scan of the lanes' totals finds the lane whose
+// running sum reaches the target and that lane's chunk sums find its chunk
+// (where rounding leaves the target above every running sum: the last lane,
+// and chunk, with weight).  draw_finish: lanes 0..7 hold the chunk's 8
+// logits and whether each is valid; a scan of their weights picks the move
+// (else the last valid one).
+struct DrawSel {
+  int ln, kb;          // lane and chunk holding the move
+  float excl, target;  // running sum before that lane's chunk; u * total
+};
+
+template <int CH>
+__device__ __forceinline__ DrawSel draw_select(const float* part, float u, int lane) {
+  float lane_tot = 0.f;
+#pragma unroll
+  for (int k = 0; k < CH; ++k) lane_tot += part[k];
+  float incl = lane_tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  DrawSel d;
+  d.target = u * __shfl_sync(0xffffffffu, incl, 31);
+  const unsigned hit = __ballot_sync(0xffffffffu, lane_tot > 0.f && incl >= d.target);
+  const unsigned withw = __ballot_sync(0xffffffffu, lane_tot > 0.f);
+  d.ln = hit ? __ffs(hit) - 1 : 31 - __clz(withw);
+  // every lane finds the chunk it would take; lane ln's answer is used
+  float run = incl - lane_tot, before = 0.f, last_before = 0.f;
+  int kc = -1, klast = 0;
+#pragma unroll
+  for (int k = 0; k < CH; ++k) {
+    if (part[k] > 0.f) {
+      klast = k;
+      last_before = run;
+      if (kc < 0 && run + part[k] >= d.target) {
+        kc = k;
+        before = run;
+      }
+    }
+    if (kc < 0) run += part[k];
+  }
+  if (kc < 0) {
+    kc = klast;
+    before = last_before;
+  }
+  d.kb = __shfl_sync(0xffffffffu, kc, d.ln);
+  d.excl = __shfl_sync(0xffffffffu, before, d.ln);
+  return d;
+}
+
+__device__ __forceinline__ int draw_finish(const DrawSel& d, float zi, bool vi, float shift2,
+                                           int lane) {
+  const int li = lane & 7;
+  float sc = vi ? exp_shifted(zi, shift2) : 0.f;
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    const float v = __shfl_up_sync(0xffffffffu, sc, o, 8);
+    if (li >= o) sc += v;
+  }
+  const unsigned hit8 = __ballot_sync(0xffffffffu, vi && d.excl + sc >= d.target);
+  const unsigned val8 = __ballot_sync(0xffffffffu, vi);
+  return hit8 ? __ffs(hit8) - 1 : 31 - __clz(val8);
 }
 
 __global__ void lt_init_kernel(LearnedDev d) {
@@ -220,274 +304,325 @@ __global__ void lt_init_kernel(LearnedDev d) {
   d.lor[c] = l;
 }
 
-// After a forward pass of the current states: keep their logits and lse.
-template <int CH>
-__global__ void __launch_bounds__(256, CH <= 4 ? 4 : 2) lt_keep_kernel(LearnedDev d, MoveTable mt,
-                                                                      const __nv_bfloat16* Z) {
-  __shared__ MoveMaps mm;
-  __shared__ unsigned s_bits[8][kLtChunks * 8];
-  build_move_maps(mt, mm, 0);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int c = blockIdx.x * 8 + w; c < d.B; c += gridDim.x * 8) {
-    int sa, sb;
-    load_slots(d.slots + (size_t)c * d.n, d.n, lane, sa, sb);
-    LogitRow<CH> r;
-    load_row(Z + (size_t)c * d.NMp, mt.NM, lane, r);
-    row_valid(mm, sa, sb, mt.NM, lane, s_bits[w], r);
-    const float l = row_lse(r);
-    __nv_bfloat16* zc = d.Zcur + (size_t)c * d.NMp;
-#pragma unroll
-    for (int k = 0; k < CH; ++k)
-      if (k * 256 + lane * 8 < mt.NM) *(uint4*)(zc + k * 256 + lane * 8) = r.w[k];
-    if (lane == 0) d.lse[c] = l;
-    __syncwarp();
-  }
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Asynchronous 16-byte copy global -> shared (cp.async, L2 only) and the
+// waits on this thread's own copies.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_prev() {   // all groups but the newest
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
 }
 
-// A chain's inputs to the propose kernel, loaded one chain ahead: its logit
-// row, its configuration (lanes), rung, energy and log-normaliser.
+// A chain's inputs to the step kernel, loaded one chain ahead: the proposed
+// configuration, the chain's rung, energy and proposal record, and its
+// current state's shift and log-normaliser (registers); the proposed
+// state's logit row, the current state's row and this current state's
+// stored weight sums (the warp's shared-memory staging, copied
+// asynchronously; nothing here waits for a load).  first: only the proposed
+// (initial) rows exist.
 template <int CH>
-struct ProposeIn {
-  LogitRow<CH> r;
+struct StepIn {
   int sa, sb, rung, E;
-  float lse;
-};
-
-template <int CH>
-__device__ __forceinline__ void load_propose_in(const LearnedDev& d, int NM, int c, int lane,
-                                                ProposeIn<CH>& in) {
-  load_row(d.Zcur + (size_t)c * d.NMp, NM, lane, in.r);
-  load_slots(d.slots + (size_t)c * d.n, d.n, lane, in.sa, in.sb);
-  in.rung = d.rung[c];
-  in.E = d.E[c];
-  in.lse = d.lse[c];
-}
-
-// Statistics of iteration t, then a move drawn from the current softmax; the
-// proposed configuration goes to `prop_slots`, and its bin occupancies
-// straight into the network's input rows X ([B][K1] bf16), so the forward
-// that follows needs no input kernel.  The draw is an inverse CDF over the
-// valid moves in move order, from the row in registers: the chunk sums
-// (warp reductions), the chunk that holds u * total, a scan of its lanes'
-// sums, then the lane that holds it walks its 8 moves.  The proposal record
-// carries the move, dE, log q(C' | C) and the uniform word of the
-// acceptance test (the same Philox block, word 1), so the accept kernel
-// computes no Philox block of its own.  Each warp loads the next chain's row
-// and state while it works on the current one.
-template <int CH>
-__global__ void __launch_bounds__(256, CH <= 4 ? 3 : 2)
-    lt_propose_kernel(LearnedDev d, MoveTable mt, unsigned t, int count_stats,
-                      unsigned char* prop_slots, __nv_bfloat16* X, int K1) {
-  __shared__ MoveMaps mm;
-  __shared__ int s_occ[8][2 * kPtMaxN];
-  __shared__ unsigned s_bits[8][kLtChunks * 8];
-  build_move_maps(mt, mm, CH * 256);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int NM = mt.NM, stride = gridDim.x * 8;
-  int c = blockIdx.x * 8 + w;
-  ProposeIn<CH> cur;
-  if (c < d.B) load_propose_in(d, NM, c, lane, cur);
-  for (; c < d.B; c += stride) {
-    ProposeIn<CH> nxt;
-    if (c + stride < d.B) load_propose_in(d, NM, c + stride, lane, nxt);
-    const int ladder = c / d.M, rg = cur.rung;
-    if (lane == 0 && count_stats)
-      atomicAdd(&d.hist[((size_t)ladder * d.M + rg) * d.nb + cur.E], 1u);
-    place_occupancy(cur.sa, cur.sb, d.n, d.delta, s_occ[w], lane);
-    LogitRow<CH>& r = cur.r;
-    row_valid(mm, cur.sa, cur.sb, NM, lane, s_bits[w], r);
-    const float lse = cur.lse;
-    const uint4 rw = philox4x32_10_rk(make_uint4(t, (unsigned)rg, (unsigned)ladder, 5u), d.rk);
-    // per lane and chunk: the sum of exp(z - lse) over its valid moves
-    const float lse2 = lse * 1.4426950408889634f;
-    float part[CH], csum[CH];
-    float total = 0.f;
-#pragma unroll
-    for (int k = 0; k < CH; ++k) {
-      float a = 0.f;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float e = exp_shifted(row_elem(r.w[k], i), lse2);
-        a += ((r.valid[k] >> i) & 1u) ? e : 0.f;
-      }
-      part[k] = a;
-      csum[k] = warp_sum(a);
-      total += csum[k];
-    }
-    const float target = ((float)rw.x + 0.5f) * 2.3283064365386963e-10f * total;
-    // the chunk: the first whose running sum reaches the target (the last
-    // one with valid moves if rounding leaves the target above the total)
-    float run = 0.f, pk = 0.f;
-    uint4 wk = make_uint4(0, 0, 0, 0);
-    unsigned vk = 0;
-    int kc = -1, klast = 0;
-#pragma unroll
-    for (int k = 0; k < CH; ++k) {
-      const bool any = __any_sync(0xffffffffu, r.valid[k] != 0u);
-      if (any) klast = k;
-      if (kc < 0 && any && run + csum[k] >= target) {
-        kc = k;
-      } else if (kc < 0) {
-        run += csum[k];
-      }
-    }
-    if (kc < 0) {                          // rounding: take the last chunk with valid moves
-      kc = klast;
-      run = total;                         // every lane of that chunk then falls through to its last move
-#pragma unroll
-      for (int k = 0; k < CH; ++k)
-        if (k == klast) run -= csum[k];
-    }
-#pragma unroll
-    for (int k = 0; k < CH; ++k)
-      if (k == kc) { pk = part[k]; wk = r.w[k]; vk = r.valid[k]; }
-    // lanes of the chunk: inclusive scan of their sums
-    float incl = pk;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const float u = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += u;
-    }
-    const unsigned hit = __ballot_sync(0xffffffffu, vk != 0u && run + incl >= target);
-    const unsigned withv = __ballot_sync(0xffffffffu, vk != 0u);
-    const int ln = hit ? __ffs(hit) - 1 : 31 - __clz(withv);   // withv != 0: the chunk has valid moves
-    // that lane's 8 moves, one a lane on lanes 0..7: the running sum before
-    // them, a scan of their terms, the first that reaches the target (else
-    // its last valid move)
-    const float excl = __shfl_sync(0xffffffffu, run + incl - pk, ln);
-    const unsigned vl = __shfl_sync(0xffffffffu, vk, ln);
-    const uint4 wp = make_uint4(__shfl_sync(0xffffffffu, wk.x, ln), __shfl_sync(0xffffffffu, wk.y, ln),
-                                __shfl_sync(0xffffffffu, wk.z, ln), __shfl_sync(0xffffffffu, wk.w, ln));
-    const int li = lane & 7;
-    const bool vi = lane < 8 && ((vl >> li) & 1u);
-    float sc = vi ? exp_shifted(row_elem(wp, li), lse2) : 0.f;
-#pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-      const float u = __shfl_up_sync(0xffffffffu, sc, o, 8);
-      if (li >= o) sc += u;
-    }
-    const unsigned hit8 = __ballot_sync(0xffffffffu, vi && excl + sc >= target);
-    const unsigned val8 = __ballot_sync(0xffffffffu, vi);
-    const int pick_i = hit8 ? __ffs(hit8) - 1 : 31 - __clz(val8);
-    const int pick = kc * 256 + ln * 8 + pick_i;
-    const int kp = mm.k[pick];
-    const int s_new = mm.s[pick], s_old = slot_of(cur.sa, cur.sb, kp);
-    const int dk = kp + d.delta;
-    const int dE = move_delta_e(s_occ[w], s_old, dk, s_new);
-    unsigned char* ps = prop_slots + (size_t)c * d.n;
-    if (cur.sa >= 0) ps[lane] = (unsigned char)(lane + 1 == kp ? s_new : cur.sa);
-    if (cur.sb >= 0) ps[lane + 32] = (unsigned char)(lane + 33 == kp ? s_new : cur.sb);
-    if (lane == 0) {
-      d.prop[c] = make_int4(kp | (s_old << 8) | (s_new << 16), dE,
-                            __float_as_int(row_elem(wp, pick_i) - lse), (int)rw.y);
-      // the proposed configuration's occupancies
-      s_occ[w][s_old] -= 1;
-      s_occ[w][s_old + dk] -= 1;
-      s_occ[w][s_new] += 1;
-      s_occ[w][s_new + dk] += 1;
-    }
-    __syncwarp();
-    // its network input row: four adjacent bf16 occupancies a lane (one
-    // 8-byte store; bins beyond 2n are 0)
-    for (int col = lane * 4; col < K1; col += 128) {
-      unsigned short h[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        h[i] = __bfloat16_as_ushort(
-            __float2bfloat16(col + i < 2 * d.n ? (float)s_occ[w][col + i] : 0.f));
-      *(uint2*)(X + (size_t)c * K1 + col) =
-          make_uint2((unsigned)h[0] | ((unsigned)h[1] << 16), (unsigned)h[2] | ((unsigned)h[3] << 16));
-    }
-    __syncwarp();
-    cur = nxt;
-  }
-}
-
-// A chain's inputs to the accept kernel, loaded one chain ahead: the
-// proposed state's logit row and configuration, the rung and the proposal
-// record.
-template <int CH>
-struct AcceptIn {
-  LogitRow<CH> r;
-  int sa, sb, rung;
+  float lse, mx;
   int4 pr;
 };
 
 template <int CH>
-__device__ __forceinline__ void load_accept_in(const LearnedDev& d, const __nv_bfloat16* Zp,
-                                               const unsigned char* prop_slots, int NM, int c,
-                                               int lane, AcceptIn<CH>& in) {
-  load_row(Zp + (size_t)c * d.NMp, NM, lane, in.r);
-  load_slots(prop_slots + (size_t)c * d.n, d.n, lane, in.sa, in.sb);
-  in.rung = d.rung[c];
-  in.pr = d.prop[c];
+struct StepBuf {
+  uint4 row[CH * 32];      // proposed state's logits, lane l's words at l, l + 32, ...
+  uint4 crow[CH * 32];     // current state's logits
+  float part[CH * 32];     // current state's weight sums
+};
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
 }
 
-// Metropolis-Hastings acceptance with the proposed states' logits Zp (bf16):
-// the log-normaliser of the proposed row and its logit of the reverse move
-// (taken from the lane that holds it), then the decision with the uniform
-// word the propose kernel drew; an accepted state keeps its row as the
-// chain's current logits.  Each warp loads the next chain's inputs while it
-// works on the current one.
 template <int CH>
-__global__ void __launch_bounds__(256, CH <= 4 ? 3 : 2)
-    lt_accept_kernel(LearnedDev d, MoveTable mt, unsigned t, const unsigned char* prop_slots,
-                     const __nv_bfloat16* Zp) {
-  __shared__ MoveMaps mm;
-  __shared__ unsigned s_bits[8][kLtChunks * 8];
-  __shared__ double s_beta[kPtMaxRungsLearned];
-  build_move_maps(mt, mm, 0);
-  for (int i = threadIdx.x; i < d.M; i += blockDim.x) s_beta[i] = d.beta[i];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int NM = mt.NM, stride = gridDim.x * 8;
-  int c = blockIdx.x * 8 + w;
-  AcceptIn<CH> cur;
-  if (c < d.B) load_accept_in(d, Zp, prop_slots, NM, c, lane, cur);
-  for (; c < d.B; c += stride) {
-    AcceptIn<CH> nxt;
-    if (c + stride < d.B) load_accept_in(d, Zp, prop_slots, NM, c + stride, lane, nxt);
-    const int ladder = c / d.M, rg = cur.rung;
-    LogitRow<CH>& r = cur.r;
-    row_valid(mm, cur.sa, cur.sb, NM, lane, s_bits[w], r);
-    const float lse_p = row_lse(r);
-    // the reverse move (k, old slot): chunk, lane and element that hold it
-    const int kp = cur.pr.x & 0xFF, s_old = (cur.pr.x >> 8) & 0xFF, dE = cur.pr.y;
-    const int idx = mm.off[kp] + s_old;
-    const int kc = idx >> 8, ln = (idx & 255) >> 3, ei = idx & 7;
-    uint4 wk = make_uint4(0, 0, 0, 0);
+__device__ __forceinline__ void load_step_in(const LearnedDev& d, const __nv_bfloat16* Zp,
+                                             const unsigned char* prop_slots, int NM, int c,
+                                             int lane, bool first, StepBuf<CH>& buf,
+                                             StepIn<CH>& in) {
+  load_slots(prop_slots + (size_t)c * d.n, d.n, lane, in.sa, in.sb);
+  in.rung = d.rung[c];
+  in.E = d.E[c];
+  const __nv_bfloat16* z = Zp + (size_t)c * d.NMp;
 #pragma unroll
-    for (int k = 0; k < CH; ++k)
-      if (k == kc) wk = r.w[k];
-    const uint4 wr = make_uint4(__shfl_sync(0xffffffffu, wk.x, ln), __shfl_sync(0xffffffffu, wk.y, ln),
-                                __shfl_sync(0xffffffffu, wk.z, ln), __shfl_sync(0xffffffffu, wk.w, ln));
-    const float lq_rev = row_elem(wr, ei) - lse_p;
-    const float log_a = (float)(-s_beta[rg] * (double)dE) + lq_rev - __int_as_float(cur.pr.z);
-    const float u = ((float)(unsigned)cur.pr.w + 0.5f) * 2.3283064365386963e-10f;
-    const bool acc = log_a >= 0.f || logf(u) < log_a;
-    if (acc) {
-      unsigned char* sl = d.slots + (size_t)c * d.n;
-      if (cur.sa >= 0) sl[lane] = (unsigned char)cur.sa;
-      if (cur.sb >= 0) sl[lane + 32] = (unsigned char)cur.sb;
-      __nv_bfloat16* zc = d.Zcur + (size_t)c * d.NMp;
+  for (int k = 0; k < CH; ++k)
+    if (k * 256 + lane * 8 < NM) cp_async16(&buf.row[k * 32 + lane], z + k * 256 + lane * 8);
+  if (!first) {
+    const __nv_bfloat16* zc = d.Zcur + (size_t)c * d.NMp;
+    const float* pp = d.parts + (size_t)c * CH * 32 + lane;
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+      if (k * 256 + lane * 8 < NM) cp_async16(&buf.crow[k * 32 + lane], zc + k * 256 + lane * 8);
+      cp_async4(&buf.part[k * 32 + lane], pp + k * 32);
+    }
+    in.lse = d.lse[c];
+    in.mx = d.mx[c];
+    in.pr = d.prop[c];
+  }
+  cp_async_commit();
+}
+
+// One chain step after the network's forward over the proposed states (one
+// warp a chain; the next chain's inputs are fetched while the warp works).
+//   * Iteration t + 1's draw is keyed by the configuration (its index l in
+//     the ladder), not by its rung, so it may precede iteration t's
+//     exchanges: Philox (t + 1, l, ladder, 5), word 0 the draw, word 1 the
+//     next test's uniform; lane j computes the block of the warp's j-th
+//     chain.
+//   * The Metropolis-Hastings test, unless the bound rejects the move
+//     outright (see the loop):
+//     the proposed row's shift (its largest element; the maximum over the
+//     valid moves if that leaves every weight below 1e-30), this lane's sums
+//     of e^(z - shift) over its valid moves, the log-normaliser, the reverse
+//     move's logit from the lane that holds it, and min(1, e^(-beta dE)
+//     q(C | C') / q(C' | C)) against the uniform drawn with the proposal.
+//     An accepted state becomes the chain's current state (configuration,
+//     row, sums, shift, log-normaliser stored) and the draw runs on its sums
+//     and row in registers; after a rejection it runs on the current
+//     state's stored weight sums (lane and chunk), then lanes 0..7 take that
+//     chunk's 8 logits from the staged current row.
+//   * The drawn move's dE, its record (move, dE, log q, the next test's
+//     uniform word), the proposed configuration and its network input row
+//     are written for the next forward.
+// first: the states in Zp are the chains' initial ones, taken unconditionally
+// (nothing to test; nothing is stored yet), and the draw is iteration 0's;
+// count0 counts their energies as iteration 0's statistics.  propose = 0: no
+// draw (the last iteration).  Dynamic shared memory: two row buffers per warp
+// (lt_step_smem).
+template <int CH>
+__host__ __device__ constexpr int lt_step_smem() {
+  return 8 * 2 * (int)sizeof(StepBuf<CH>);
+}
+
+template <int CH>
+__global__ void __launch_bounds__(256, CH <= 3 ? 3 : 2)
+    lt_step_kernel(LearnedDev d, MoveTable mt, unsigned t, int first, int propose, int count0,
+                   unsigned char* prop_slots, const __nv_bfloat16* Zp, __nv_bfloat16* X, int K1) {
+  __shared__ MoveMaps mm;
+  __shared__ int s_occ[8][2 * kPtMaxN];
+  __shared__ unsigned s_bits[8][kLtChunks * 8];
+  __shared__ float s_beta[kPtMaxRungsLearned];
+  extern __shared__ __align__(16) unsigned char s_dyn[];   // [warp][2] StepBuf
+  build_move_maps(mt, mm, CH * 256);
+  for (int i = threadIdx.x; i < d.M; i += blockDim.x) s_beta[i] = (float)d.beta[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, li = lane & 7;
+  const int NM = mt.NM, stride = gridDim.x * 8;
+  const bool fst = first != 0;
+  const unsigned tn = fst ? 0u : t + 1u;             // the iteration whose move is drawn
+  StepBuf<CH>* wbuf = (StepBuf<CH>*)s_dyn + 2 * w;
+  int c = blockIdx.x * 8 + w;
+  StepIn<CH> cur;
+  if (c < d.B) load_step_in(d, Zp, prop_slots, NM, c, lane, fst, wbuf[0], cur);
+  unsigned rwx = 0, rwy = 0;                         // Philox words of the warp's chain j0 + lane
+  for (int j = 0; c < d.B; c += stride, ++j) {
+    if ((j & 31) == 0 && propose) {
+      const int cc = c + lane * stride;
+      if (cc < d.B) {
+        const int lc = cc / d.M;
+        const uint4 rw = philox4x32_10_rk(make_uint4(tn, (unsigned)(cc - lc * d.M), (unsigned)lc, 5u), d.rk);
+        rwx = rw.x;
+        rwy = rw.y;
+      }
+    }
+    const unsigned rx = __shfl_sync(0xffffffffu, rwx, j & 31);
+    const unsigned ry = __shfl_sync(0xffffffffu, rwy, j & 31);
+    StepIn<CH> nxt;
+    if (c + stride < d.B)
+      load_step_in(d, Zp, prop_slots, NM, c + stride, lane, fst, wbuf[(j + 1) & 1], nxt);
+    else
+      cp_async_commit();                             // keep one group per chain
+    const int ladder = c / d.M, rg = cur.rung;
+    int sa = cur.sa, sb = cur.sb;
+    const float u = ((float)rx + 0.5f) * 2.3283064365386963e-10f;
+    // the draw in case of rejection: lane, chunk, and that chunk's logits
+    StepBuf<CH>& sbuf = wbuf[j & 1];
+    cp_async_wait_prev();                            // this chain's staged rows and sums
+    // whether the test needs the proposed row: the reverse move is valid in
+    // the proposed state, so log q(C | C') <= 0 and log a <= -beta dE -
+    // log q(C' | C); a uniform with log u at or above that bound (plus 1e-3
+    // of rounding slack) rejects without it
+    bool full = true;
+    if (!fst) {
+      const float ua = ((float)(unsigned)cur.pr.w + 0.5f) * 2.3283064365386963e-10f;
+      const float bound = -s_beta[cur.rung] * (float)cur.pr.y - __int_as_float(cur.pr.z);
+      full = __logf(ua) < bound + 1e-3f;
+    }
+    const int kp = cur.pr.x & 0xFF, s_old = (cur.pr.x >> 8) & 0xFF;
+    bool acc = fst;
+    int E = cur.E;
+    LogitRow<CH> r;
+    float part[CH], mx = 0.f, lse_p = 0.f;
+    if (full) {
 #pragma unroll
       for (int k = 0; k < CH; ++k)
-        if (k * 256 + lane * 8 < NM) *(uint4*)(zc + k * 256 + lane * 8) = r.w[k];
+        r.w[k] = k * 256 + lane * 8 < NM ? sbuf.row[k * 32 + lane]
+                                         : make_uint4(0xFF80FF80u, 0xFF80FF80u, 0xFF80FF80u, 0xFF80FF80u);
+      row_valid(mm, sa, sb, NM, lane, s_bits[w], r);
+      mx = row_max_all(r);
+      float total = warp_sum(row_parts(r, mx * kLog2e, part));
+      if (!(total > 1e-30f)) {
+        // rare: the valid moves' maximum instead, in rolled loops over the
+        // staged row (few live registers)
+        float m2 = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+          const unsigned short* h = (const unsigned short*)&sbuf.row[k * 32 + lane];
+#pragma unroll 1
+          for (int i = 0; i < 8; ++i)
+            if ((r.valid[k] >> i) & 1u) m2 = fmaxf(m2, __uint_as_float((unsigned)h[i] << 16));
+        }
+        mx = warp_max(m2);
+        total = 0.f;
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+          const unsigned short* h = (const unsigned short*)&sbuf.row[k * 32 + lane];
+          float a = 0.f;
+#pragma unroll 1
+          for (int i = 0; i < 8; ++i)
+            if ((r.valid[k] >> i) & 1u)
+              a += exp_shifted(__uint_as_float((unsigned)h[i] << 16), mx * kLog2e);
+          part[k] = a;
+          total += a;
+        }
+        total = warp_sum(total);
+      }
+      lse_p = mx + __logf(total);
+      if (!fst) {
+        const int dE = cur.pr.y;
+        const int idx = mm.off[kp] + s_old;          // the reverse move
+        const int kc = idx >> 8, ln = (idx & 255) >> 3, ei = idx & 7;
+        uint4 wk = r.w[0];
+#pragma unroll
+        for (int k = 1; k < CH; ++k)
+          if (k == kc) wk = r.w[k];
+        const uint4 wr = make_uint4(__shfl_sync(0xffffffffu, wk.x, ln), __shfl_sync(0xffffffffu, wk.y, ln),
+                                    __shfl_sync(0xffffffffu, wk.z, ln), __shfl_sync(0xffffffffu, wk.w, ln));
+        const float lq_rev = row_elem(wr, ei) - lse_p;
+        const float log_a = -s_beta[rg] * (float)dE + lq_rev - __int_as_float(cur.pr.z);
+        const float ua = ((float)(unsigned)cur.pr.w + 0.5f) * 2.3283064365386963e-10f;
+        acc = log_a >= 0.f || __logf(ua) < log_a;
+        if (acc) {
+          E += dE;
+          unsigned char* sl = d.slots + (size_t)c * d.n;
+          if (sa >= 0) sl[lane] = (unsigned char)sa;
+          if (sb >= 0) sl[lane + 32] = (unsigned char)sb;
+          if (lane == 0) {
+            d.E[c] = E;
+            d.accm[(size_t)ladder * d.M + rg] += 1u;   // one configuration a rung and ladder
+          }
+        }
+      } else if (count0 && lane == 0) {
+        d.hist[((size_t)ladder * d.M + rg) * d.nb + E] += 1u;
+      }
+      if (acc) {                                     // store the new current state
+        __nv_bfloat16* zc = d.Zcur + (size_t)c * d.NMp;
+        float* pp = d.parts + (size_t)c * CH * 32 + lane;
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+          if (k * 256 + lane * 8 < NM) *(uint4*)(zc + k * 256 + lane * 8) = r.w[k];
+          pp[k * 32] = part[k];
+        }
+        if (lane == 0) {
+          d.lse[c] = lse_p;
+          d.mx[c] = mx;
+        }
+      }
+    }
+    if (propose) {
+      int pick;
+      float zq, lse_c;
+      if (acc) {
+        const DrawSel sel = draw_select<CH>(part, u, lane);
+        uint4 wk = r.w[0];
+        unsigned vk = r.valid[0];
+#pragma unroll
+        for (int k = 1; k < CH; ++k)
+          if (k == sel.kb) {
+            wk = r.w[k];
+            vk = r.valid[k];
+          }
+        const unsigned vl = __shfl_sync(0xffffffffu, vk, sel.ln);
+        const uint4 wp = make_uint4(__shfl_sync(0xffffffffu, wk.x, sel.ln), __shfl_sync(0xffffffffu, wk.y, sel.ln),
+                                    __shfl_sync(0xffffffffu, wk.z, sel.ln), __shfl_sync(0xffffffffu, wk.w, sel.ln));
+        const float zi = row_elem(wp, li);
+        const int pi = draw_finish(sel, zi, lane < 8 && ((vl >> li) & 1u), mx * kLog2e, lane);
+        zq = __shfl_sync(0xffffffffu, zi, pi);
+        pick = sel.kb * 256 + sel.ln * 8 + pi;
+        lse_c = lse_p;
+      } else {
+        // back to the current state (pair kp at its old slot); lanes 0..7
+        // test whether their move of the drawn chunk is valid there (inside
+        // the table, and not the pair's current slot)
+        if (lane + 1 == kp) sa = s_old;
+        if (lane + 33 == kp) sb = s_old;
+        float cpart[CH];
+#pragma unroll
+        for (int k = 0; k < CH; ++k) cpart[k] = sbuf.part[k * 32 + lane];
+        const DrawSel rej = draw_select<CH>(cpart, u, lane);
+        const float zrej = __uint_as_float(
+            (unsigned)((const unsigned short*)&sbuf.crow[rej.kb * 32 + rej.ln])[li] << 16);
+        const int m = rej.kb * 256 + rej.ln * 8 + li;
+        const int km = m < NM ? mm.k[m] : 1;
+        const int cs = slot_of_lanes(sa, sb, km);
+        const bool vi = lane < 8 && m < NM && cs != (int)mm.s[m];
+        const int pi = draw_finish(rej, zrej, vi, cur.mx * kLog2e, lane);
+        zq = __shfl_sync(0xffffffffu, zrej, pi);
+        pick = rej.kb * 256 + rej.ln * 8 + pi;
+        lse_c = cur.lse;
+      }
+      place_occupancy(sa, sb, d.n, d.delta, s_occ[w], lane);
+      const int kq = mm.k[pick], q_new = mm.s[pick], q_old = slot_of(sa, sb, kq);
+      const int dk = kq + d.delta;
+      const int dEq = move_delta_e(s_occ[w], q_old, dk, q_new);
+      unsigned char* ps = prop_slots + (size_t)c * d.n;
+      if (sa >= 0) ps[lane] = (unsigned char)(lane + 1 == kq ? q_new : sa);
+      if (sb >= 0) ps[lane + 32] = (unsigned char)(lane + 33 == kq ? q_new : sb);
       if (lane == 0) {
-        d.lse[c] = lse_p;
-        atomicAdd(&d.E[c], dE);
-        atomicAdd(&d.accm[(size_t)ladder * d.M + rg], 1u);
+        d.prop[c] = make_int4(kq | (q_old << 8) | (q_new << 16), dEq, __float_as_int(zq - lse_c),
+                              (int)ry);
+        // the proposed configuration's occupancies
+        s_occ[w][q_old] -= 1;
+        s_occ[w][q_old + dk] -= 1;
+        s_occ[w][q_new] += 1;
+        s_occ[w][q_new + dk] += 1;
+      }
+      __syncwarp();
+      // its network input row: four adjacent bf16 occupancies a lane (one
+      // 8-byte store; a count below 256 is exact in bf16, its float's upper
+      // half), the columns of the 2n bins only -- the rest of the row stays
+      // 0 from the initial states' input rows
+      for (int col = lane * 4; col < 2 * d.n; col += 128) {
+        unsigned h[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          h[i] = col + i < 2 * d.n ? __float_as_uint((float)s_occ[w][col + i]) >> 16 : 0u;
+        *(uint2*)(X + (size_t)c * K1 + col) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
       }
     }
     __syncwarp();
     cur = nxt;
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// Exchanges of iteration t, one warp per ladder, lane j for rung j.
-__global__ void lt_exchange_kernel(LearnedDev d, unsigned t) {
+// Exchanges of iteration t, one warp per ladder, lane j for rung j; count:
+// the energies the rungs hold afterwards are iteration t + 1's statistics.
+__global__ void lt_exchange_kernel(LearnedDev d, unsigned t, int count) {
   const int lane = threadIdx.x & 31;
   const int ladder = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (ladder >= d.L) return;
@@ -495,7 +630,7 @@ __global__ void lt_exchange_kernel(LearnedDev d, unsigned t) {
   int* lor = d.lor + (size_t)ladder * M;
   const int my = lane < M ? lor[lane] : 0;
   const int Er = lane < M ? d.E[(size_t)ladder * M + my] : 0;
-  const int En = __shfl_down_sync(0xffffffffu, Er, 1);
+  const int En = __shfl_down_sync(0xffffffffu, Er, 1), Eu = __shfl_up_sync(0xffffffffu, Er, 1);
   int dec = 0;
   if (lane + 1 < M && (lane & 1) == (int)(t & 1u)) {
     const uint4 w = philox4x32_10(make_uint4(t, (unsigned)lane, (unsigned)ladder, 3u), d.key0,
@@ -506,10 +641,13 @@ __global__ void lt_exchange_kernel(LearnedDev d, unsigned t) {
   }
   const int down = __shfl_down_sync(0xffffffffu, my, 1), up = __shfl_up_sync(0xffffffffu, my, 1);
   const int dec_up = __shfl_up_sync(0xffffffffu, dec, 1);
-  const int nl = dec ? down : ((lane > 0 && dec_up) ? up : my);
+  const bool from_up = lane > 0 && dec_up;
+  const int nl = dec ? down : (from_up ? up : my);
+  const int nE = dec ? En : (from_up ? Eu : Er);
   if (lane < M) {
     lor[lane] = nl;
     d.rung[(size_t)ladder * M + nl] = lane;
+    if (count) d.hist[((size_t)ladder * M + lane) * d.nb + nE] += 1u;
   }
 }
 
@@ -530,14 +668,14 @@ namespace sk {
 #define SK_LT_CHUNKS(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
 static_assert(kLtChunks == 10, "one case per chunk count");
 struct LtKernels {
-  void (*keep)(LearnedDev, MoveTable, const __nv_bfloat16*);
-  void (*propose)(LearnedDev, MoveTable, unsigned, int, unsigned char*, __nv_bfloat16*, int);
-  void (*accept)(LearnedDev, MoveTable, unsigned, const unsigned char*, const __nv_bfloat16*);
+  void (*step)(LearnedDev, MoveTable, unsigned, int, int, int, unsigned char*,
+               const __nv_bfloat16*, __nv_bfloat16*, int);
+  int smem;                      // the step kernel's dynamic shared memory
 };
 static bool lt_kernels(int ch, LtKernels* k) {
   switch (ch) {
 #define SK_LT_CASE(c) \
-  case c: *k = {lt_keep_kernel<c>, lt_propose_kernel<c>, lt_accept_kernel<c>}; return true;
+  case c: *k = {lt_step_kernel<c>, lt_step_smem<c>()}; return true;
     SK_LT_CHUNKS(SK_LT_CASE)
 #undef SK_LT_CASE
     default: return false;
@@ -586,6 +724,9 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
   const size_t o_lor = off; off = al(off + (size_t)B * 4);
   const size_t o_z = off; off = al(off + (size_t)B * m->NMp * 2);
   const size_t o_lse = off; off = al(off + (size_t)B * 4);
+  const size_t o_mx = off; off = al(off + (size_t)B * 4);
+  const int CHn = (m->NMp + 255) / 256;   // >= the move table's chunks
+  const size_t o_pa = off; off = al(off + (size_t)B * CHn * 32 * 4);
   const size_t o_pr = off; off = al(off + (size_t)B * 16);
   const size_t o_h = off; off = al(off + (size_t)L * M * nb * 4);
   const size_t o_am = off; off = al(off + (size_t)L * M * 4);
@@ -605,6 +746,8 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
   d.lor = (int*)(p + o_lor);
   d.Zcur = (__nv_bfloat16*)(p + o_z);
   d.lse = (float*)(p + o_lse);
+  d.mx = (float*)(p + o_mx);
+  d.parts = (float*)(p + o_pa);
   d.prop = (int4*)(p + o_pr);
   d.hist = (unsigned*)(p + o_h);
   d.accm = (unsigned*)(p + o_am);
@@ -620,7 +763,8 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
     return SK_EINVAL;
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  e = cudaMemsetAsync(p + o_h, 0, o_b - o_h, s);
+  e = cudaFuncSetAttribute((const void*)lk.step, cudaFuncAttributeMaxDynamicSharedMemorySize, lk.smem);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p + o_h, 0, o_b - o_h, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p + o_b, beta, (size_t)M * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p + o_ts, ts.data(), ts.size() * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->slots, 0, (size_t)Bp * n, s);   // padding rows
@@ -632,18 +776,21 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
     e = cudaMemcpyAsync(m->slots, d.slots, (size_t)B * n, cudaMemcpyDeviceToDevice, s);
   }
   const __nv_bfloat16* Zb = (const __nv_bfloat16*)m->Z;      // the forward's bf16 logits
+  // the initial states' forward, then their rows kept and iteration 0's draw
   if (e == cudaSuccess) e = mlp_forward_dev(*m, Bp, s, true);
   if (e == cudaSuccess) {
-    lk.keep<<<chain_grid, 256, 0, s>>>(d, mt, Zb);
+    lk.step<<<chain_grid, 256, lk.smem, s>>>(d, mt, 0u, 1, iters > 0 ? 1 : 0,
+                                       iters > 0 && burnin == 0 ? 1 : 0, m->slots, Zb, m->X, m->K1);
     e = cudaGetLastError();
   }
   for (uint64_t t = 0; t < iters && e == cudaSuccess; ++t) {
-    lk.propose<<<chain_grid, 256, 0, s>>>(d, mt, (unsigned)t, t >= burnin ? 1 : 0, m->slots, m->X,
-                                          m->K1);
-    e = mlp_forward_dev(*m, Bp, s, true, true);     // propose wrote the input rows
+    e = mlp_forward_dev(*m, Bp, s, true, true);     // the step kernel wrote the input rows
     if (e != cudaSuccess) break;
-    lk.accept<<<chain_grid, 256, 0, s>>>(d, mt, (unsigned)t, m->slots, Zb);
-    lt_exchange_kernel<<<(L + 3) / 4, 128, 0, s>>>(d, (unsigned)t);
+    const bool more = t + 1 < iters;
+    lk.step<<<chain_grid, 256, lk.smem, s>>>(d, mt, (unsigned)t, 0, more ? 1 : 0, 0, m->slots, Zb, m->X,
+                                       m->K1);
+    lt_exchange_kernel<<<(L + 3) / 4, 128, 0, s>>>(d, (unsigned)t,
+                                                   more && t + 1 >= burnin ? 1 : 0);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
