@@ -41,37 +41,37 @@ struct LearnedDev {
   unsigned* accm;            // [L][M]
   unsigned* accs;            // [L][M]
   const double* beta;        // [M]
+  const struct MoveMaps* maps;   // the move layout tables (host_move_maps)
   const unsigned long long* tswap;   // [M][nb]
 };
 
 // Per-block tables of the move layout: the pair k and the start slot of
 // every move m (moves of pair k are off[k] .. off[k+1]-1), read for the one
-// move a chain draws; and the offsets off[k] themselves.
+// move a chain draws; and the offsets off[k] themselves.  Built once per run
+// on the host (host_move_maps; padding moves are pair 0, slot 0), kept in
+// global memory and copied into each block's shared memory.
 constexpr int kMaxMoves = 2560;        // sum_k (2n - d_k) for n <= kMlpMaxN, padded to 256
 struct MoveMaps {
   __align__(16) unsigned char k[kMaxMoves];
   __align__(16) unsigned char s[kMaxMoves];
-  int off[kPtMaxN + 2];
+  __align__(16) int off[kPtMaxN + 4];
 };
+static_assert(sizeof(MoveMaps) % 16 == 0, "copied in 16-byte words");
 
-// The first `moves` entries of the tables (the chunks a kernel covers).
-__device__ __forceinline__ void build_move_maps(const MoveTable& mt, MoveMaps& mm, int moves) {
-  for (int k = threadIdx.x; k <= mt.n + 1; k += blockDim.x) mm.off[k] = k ? mt.off[k] : 0;
-  for (int m = threadIdx.x; m < moves; m += blockDim.x) {
-    if (m >= mt.NM) {                      // padding
-      mm.k[m] = 0;
-      mm.s[m] = 0;
-      continue;
+static void host_move_maps(const MoveTable& mt, MoveMaps* mm) {
+  std::memset(mm, 0, sizeof(*mm));
+  for (int k = 1; k <= mt.n + 1; ++k) mm->off[k] = mt.off[k];
+  for (int k = 1; k <= mt.n; ++k)
+    for (int m = mt.off[k]; m < mt.off[k + 1]; ++m) {
+      mm->k[m] = (unsigned char)k;
+      mm->s[m] = (unsigned char)(m - mt.off[k]);
     }
-    int lo = 1, hi = mt.n;                 // the pair with off[k] <= m < off[k+1]
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (mt.off[mid] <= m) lo = mid;
-      else hi = mid - 1;
-    }
-    mm.k[m] = (unsigned char)lo;
-    mm.s[m] = (unsigned char)(m - mt.off[lo]);
-  }
+}
+
+__device__ __forceinline__ void copy_move_maps(const MoveMaps* g, MoveMaps& mm) {
+  const uint4* src = (const uint4*)g;
+  uint4* dst = (uint4*)&mm;
+  for (int i = threadIdx.x; i < (int)(sizeof(MoveMaps) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
 }
 
 // A configuration in registers: lane k-1 holds the start slot of pair k,
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(256, CH <= 3 ? 3 : 2)
   __shared__ unsigned s_bits[8][kLtChunks * 8];
   __shared__ float s_beta[kPtMaxRungsLearned];
   extern __shared__ __align__(16) unsigned char s_dyn[];   // [warp][2] StepBuf
-  build_move_maps(mt, mm, CH * 256);
+  copy_move_maps(d.maps, mm);
   for (int i = threadIdx.x; i < d.M; i += blockDim.x) s_beta[i] = (float)d.beta[i];
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, li = lane & 7;
@@ -732,6 +732,7 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
   const size_t o_am = off; off = al(off + (size_t)L * M * 4);
   const size_t o_as = off; off = al(off + (size_t)L * M * 4);
   const size_t o_b = off; off = al(off + (size_t)M * 8);
+  const size_t o_mm = off; off = al(off + sizeof(MoveMaps));
   const size_t o_ts = off; off = al(off + ts.size() * 8);
   const size_t o_out = off; off = al(off + ((size_t)M * nb + 2 * M) * 8);
   char* p = nullptr;
@@ -753,6 +754,7 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
   d.accm = (unsigned*)(p + o_am);
   d.accs = (unsigned*)(p + o_as);
   d.beta = (const double*)(p + o_b);
+  d.maps = (const MoveMaps*)(p + o_mm);
   d.tswap = (const unsigned long long*)(p + o_ts);
   unsigned long long* out = (unsigned long long*)(p + o_out);
   const MoveTable mt = move_table(*m);
@@ -766,6 +768,9 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
   e = cudaFuncSetAttribute((const void*)lk.step, cudaFuncAttributeMaxDynamicSharedMemorySize, lk.smem);
   if (e == cudaSuccess) e = cudaMemsetAsync(p + o_h, 0, o_b - o_h, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p + o_b, beta, (size_t)M * 8, cudaMemcpyHostToDevice, s);
+  MoveMaps hmm;
+  host_move_maps(mt, &hmm);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p + o_mm, &hmm, sizeof(hmm), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p + o_ts, ts.data(), ts.size() * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->slots, 0, (size_t)Bp * n, s);   // padding rows
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
@@ -783,16 +788,31 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
                                        iters > 0 && burnin == 0 ? 1 : 0, m->slots, Zb, m->X, m->K1);
     e = cudaGetLastError();
   }
+  // The exchanges of iteration t run on a side stream beside the forward of
+  // iteration t + 1 (which reads only the input rows and the weights); the
+  // step kernel of t + 1 waits for them (it reads the rungs and writes the
+  // energies they read).
+  cudaStream_t xs = nullptr;
+  cudaEvent_t ev_step = nullptr, ev_exch = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&xs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_step, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_exch, cudaEventDisableTiming);
   for (uint64_t t = 0; t < iters && e == cudaSuccess; ++t) {
     e = mlp_forward_dev(*m, Bp, s, true, true);     // the step kernel wrote the input rows
+    if (e == cudaSuccess && t > 0) e = cudaStreamWaitEvent(s, ev_exch, 0);
     if (e != cudaSuccess) break;
     const bool more = t + 1 < iters;
     lk.step<<<chain_grid, 256, lk.smem, s>>>(d, mt, (unsigned)t, 0, more ? 1 : 0, 0, m->slots, Zb, m->X,
                                        m->K1);
-    lt_exchange_kernel<<<(L + 3) / 4, 128, 0, s>>>(d, (unsigned)t,
-                                                   more && t + 1 >= burnin ? 1 : 0);
-    e = cudaGetLastError();
+    e = cudaEventRecord(ev_step, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(xs, ev_step, 0);
+    if (e != cudaSuccess) break;
+    lt_exchange_kernel<<<(L + 3) / 4, 128, 0, xs>>>(d, (unsigned)t,
+                                                    more && t + 1 >= burnin ? 1 : 0);
+    e = cudaEventRecord(ev_exch, xs);
+    if (e == cudaSuccess) e = cudaGetLastError();
   }
+  if (e == cudaSuccess && iters > 0) e = cudaStreamWaitEvent(s, ev_exch, 0);
   if (e == cudaSuccess) {
     const int per = M * nb;
     lt_reduce_kernel<<<(per + 255) / 256, 256, 0, s>>>(d.hist, L, per, out);
@@ -807,6 +827,10 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
   if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess && xs) cudaStreamSynchronize(xs);   // nothing of it left in flight
+  if (ev_step) cudaEventDestroy(ev_step);
+  if (ev_exch) cudaEventDestroy(ev_exch);
+  if (xs) cudaStreamDestroy(xs);
   cudaFree(p);
   if (own) cudaStreamDestroy(s);
   if (e != cudaSuccess) return cuda_status(e);
