@@ -376,6 +376,11 @@ int sk_mlp_get_params(const void *model, float *params);   /* host, n_params */
 /* Logits of B <= max_batch states.  slots (host, B x n): start slot of pair
  * k = 1..n of each state; logits (host, B x n_moves). */
 int sk_mlp_forward(void *model, const uint8_t *slots, int B, float *logits);
+/* The same logits as the tempering chains read them: rounded to bf16
+ * (nearest even; the bit patterns, host, B x n_moves), from the forward that
+ * stores only the move table's columns.  Same arguments and errors as
+ * sk_mlp_forward. */
+int sk_mlp_forward_bf16(void *model, const uint8_t *slots, int B, uint16_t *logits);
 /* Mean loss of a batch (B a multiple of 128) and its gradient (host,
  * n_params, same layout as the parameters); the model is not updated. */
 int sk_mlp_loss_grad(void *model, const uint8_t *slots, int B, float beta_star, float *loss,

@@ -228,6 +228,7 @@ def lib():
         L.sk_mlp_set_params.argtypes = [vp, vp]
         L.sk_mlp_get_params.argtypes = [vp, vp]
         L.sk_mlp_forward.argtypes = [vp, vp, ctypes.c_int, vp]
+        L.sk_mlp_forward_bf16.argtypes = [vp, vp, ctypes.c_int, vp]
         L.sk_mlp_loss_grad.argtypes = [vp, vp, ctypes.c_int, ctypes.c_float, vp, vp]
         L.sk_mlp_get_train_state.argtypes = [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
         L.sk_mlp_set_gemm.argtypes = [vp, ctypes.c_int]
@@ -627,6 +628,17 @@ class Mlp:
         st = lib().sk_mlp_forward(self.handle, s.ctypes.data, s.shape[0], out.ctypes.data)
         if st != SK_OK:
             raise SkolemError(st, "sk_mlp_forward")
+        return out
+
+    def forward_bf16(self, slots):
+        """sk_mlp_forward_bf16: the logits as the tempering chains read them,
+        bf16 bit patterns (uint16, B x n_moves)."""
+        np = _np()
+        s = np.ascontiguousarray(slots, dtype=np.uint8)
+        out = np.zeros((s.shape[0], self.n_moves), dtype=np.uint16)
+        st = lib().sk_mlp_forward_bf16(self.handle, s.ctypes.data, s.shape[0], out.ctypes.data)
+        if st != SK_OK:
+            raise SkolemError(st, "sk_mlp_forward_bf16")
         return out
 
     def loss_grad(self, slots, beta_star: float):

@@ -59,6 +59,8 @@ struct TcGemmArgs {
   int ksplit;                     // K ranges (0 or 1: none); needs K / 64 % ksplit == 0
   const __nv_bfloat16* aux;       // kTcEpiMaskBf16: [M][ldaux], C = acc where aux > 0
   int ldaux;
+  int nvalid;                     // > 0: only columns < nvalid are wanted (the last column
+                                  // tile multiplies and stores that many, rounded up to 16)
 };
 
 __device__ __forceinline__ unsigned tc_smem_u32(const void* p) {
@@ -162,6 +164,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int groups = gridDim.x / (NT * KS);          // CTAs per (column tile, K range)
   const int nt = blockIdx.x % NT, ks = (blockIdx.x / NT) % KS, m_first = blockIdx.x / (NT * KS);
   const int kb0 = ks * nkb;                          // first K slice of this CTA
+  // columns of this CTA's tile that are multiplied (a multiple of 16)
+  const int ncols = g.nvalid > 0 ? min(kTcBN, (g.nvalid - nt * kTcBN + 15) / 16 * 16) : kTcBN;
   const int my_tiles = (m_first < MT) ? (MT - m_first + groups - 1) / groups : 0;
 
   if (threadIdx.x == 0) {
@@ -231,7 +235,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       bool ok = tc_wait(tc_smem_u32(&b_bar), 0);
-      const unsigned idesc = tc_idesc(kTcBM, kTcBN);
+      const unsigned idesc = tc_idesc(kTcBM, ncols);
       unsigned u = 0;
       int committed = -1;                            // last tile committed to acc full
       for (int t = 0; t < my_tiles && ok; ++t) {
@@ -302,7 +306,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int n0 = nt * kTcBN, row0 = mt * kTcBM + q * 32;
       const int crow0 = ks * g.M + row0;             // a K split's partial goes to its own rows
 #pragma unroll 1
-      for (int c0 = 0; c0 < kTcBN; c0 += kCols, ++slab) {
+      for (int c0 = 0; c0 < ncols; c0 += kCols, ++slab) {
         // the staging buffer of two slabs ago must have been read out
         if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
         __syncwarp();

@@ -432,6 +432,9 @@ cudaError_t gemm_tc_launch(const TcGemmArgs& g, const CUtensorMap& amap, const C
     return cudaErrorInvalidValue;
   if (!STREAMB && (g.K > kTcMaxK || KS > 1)) return cudaErrorInvalidValue;
   if (EPI == kTcEpiMaskBf16 && (!g.aux || g.ldaux % 8)) return cudaErrorInvalidValue;
+  // a narrowed last column tile keeps at least one column
+  if (g.nvalid < 0 || g.nvalid > g.N || (g.nvalid > 0 && g.nvalid <= g.N - kTcBN))
+    return cudaErrorInvalidValue;
   int dev = 0;
   cudaError_t e = tc_attributes(&dev);
   if (e != cudaSuccess) return e;
@@ -440,7 +443,8 @@ cudaError_t gemm_tc_launch(const TcGemmArgs& g, const CUtensorMap& amap, const C
   int per = sms / (NT * KS);
   if (per < 1) per = 1;
   if (per > MT) per = MT;
-  gemm_tc_kernel<EPI, STREAMB><<<per * NT * KS, kTcThreads, STREAMB ? kTcSmemStream : kTcSmem, s>>>(
+  const int grid = per * NT * KS;
+  gemm_tc_kernel<EPI, STREAMB><<<grid, kTcThreads, STREAMB ? kTcSmemStream : kTcSmem, s>>>(
       amap, bmap, cmap, g);
   return cudaGetLastError();
 }
@@ -472,6 +476,7 @@ cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s, bool logits_bf16, boo
     e = gemm_tc(t, m.tmA[1], m.tmB[1], m.tmC[1], kTcEpiReluBf16, s);
     if (e != cudaSuccess) return e;
     t.N = m.NMp; t.bias = m.b3;
+    if (logits_bf16) t.nvalid = (m.NM + 7) / 8 * 8;   // the columns tmZb stores
     return logits_bf16 ? gemm_tc(t, m.tmA[2], m.tmB[2], m.tmZb, kTcEpiBf16, s)
                        : gemm_tc(t, m.tmA[2], m.tmB[2], m.tmC[2], kTcEpiF32, s);
   }
@@ -962,6 +967,22 @@ extern "C" int sk_mlp_forward(void* model, const uint8_t* slots, int B, float* l
   if (e == cudaSuccess) e = sk::mlp_forward_dev(*m, Bp, nullptr);
   if (e == cudaSuccess)
     e = cudaMemcpy2D(logits, (size_t)m->NM * 4, m->Z, (size_t)m->NMp * 4, (size_t)m->NM * 4, B,
+                     cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return sk::cuda_status(e);
+  unsigned err = 0;
+  e = cudaMemcpy(&err, m->tc_err, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return sk::cuda_status(e);
+  return err ? SK_ETIMEOUT : SK_OK;
+}
+
+extern "C" int sk_mlp_forward_bf16(void* model, const uint8_t* slots, int B, uint16_t* logits) {
+  Mlp* m = (Mlp*)model;
+  if (!m || !slots || !logits || B < 1 || B > m->max_batch) return SK_EINVAL;
+  cudaError_t e;
+  const int Bp = sk::upload_states(*m, slots, B, nullptr, &e);
+  if (e == cudaSuccess) e = sk::mlp_forward_dev(*m, Bp, nullptr, true);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2D(logits, (size_t)m->NM * 2, m->Z, (size_t)m->NMp * 2, (size_t)m->NM * 2, B,
                      cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return sk::cuda_status(e);
   unsigned err = 0;

@@ -127,6 +127,30 @@ def test_tensor_memory_and_mma_sync_paths_agree(variant, n, batch):
     assert np.abs(a - b).max() <= 1e-2 * np.abs(b).max()
 
 
+@pytest.mark.parametrize("variant,n,batch", [(0, 20, 4096), (1, 20, 40000), (0, 12, 1024),
+                                             (0, 24, 4096), (1, 40, 1024)])
+def test_bf16_logits_of_the_chains(variant, n, batch):
+    # The tempering chains read the logits rounded to bf16 from a forward that
+    # stores only the move table's columns (the last column tile multiplies
+    # that many, rounded up to 16, instead of 256).  Every logit must be the
+    # fp32 forward's rounded to nearest: within half a bf16 step (2^-8
+    # relative) plus a little for accumulation order, on both GEMM paths.
+    # n = 20: 590 moves, a last tile of 80 columns; n = 24: 852 (96); n = 40:
+    # 2380 (80); 40000 states: ragged, several row tiles per CTA.
+    d = si.differences(variant, n)
+    model = sk.Mlp(variant, n, (batch + 127) // 128 * 128, seed=9)
+    slots = si.random_slots(12, batch, n, d)
+    for tc in (True, False):
+        model.set_gemm(tc)
+        z = model.forward(slots).astype(np.float64)
+        zb = (model.forward_bf16(slots).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+        model.check()
+        tol = 2.0 ** -8 * np.abs(z) + 1e-4 * np.abs(z).max()
+        assert (np.abs(zb - z) <= tol).all(), (tc, float(np.abs(zb - z).max()))
+        assert np.isfinite(zb).all()
+    model.close()
+
+
 @pytest.mark.parametrize("variant,n", [(0, 8), (1, 12)])
 def test_training_steps_match_adam_in_fp64(variant, n):
     # Two sk_mlp_train steps on one fixed minibatch of 256 states (given
