@@ -702,12 +702,9 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return SK_ECUDA;
     own = true;
   }
-  // the per-chain kernels loop over chains, 8 per block, 8 blocks per SM (two
-  // waves of the 4 resident ones)
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int chain_grid = std::min((B + 7) / 8, 8 * (sms > 0 ? sms : 1));
   LearnedDev d;
   std::memset(&d, 0, sizeof(d));
   d.n = n; d.delta = m->delta; d.M = M; d.L = L; d.B = B; d.nb = nb; d.NMp = m->NMp;
@@ -766,6 +763,13 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   e = cudaFuncSetAttribute((const void*)lk.step, cudaFuncAttributeMaxDynamicSharedMemorySize, lk.smem);
+  // the step kernel loops over chains, 8 per block: one wave of the blocks
+  // that fit on the device at once (no part-empty last wave)
+  int resident = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, (const void*)lk.step, 256, lk.smem);
+  const int chain_grid =
+      std::max(1, std::min((B + 7) / 8, std::max(resident, 1) * (sms > 0 ? sms : 1)));
   if (e == cudaSuccess) e = cudaMemsetAsync(p + o_h, 0, o_b - o_h, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p + o_b, beta, (size_t)M * 8, cudaMemcpyHostToDevice, s);
   MoveMaps hmm;
