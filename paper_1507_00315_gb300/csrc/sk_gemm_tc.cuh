@@ -38,7 +38,7 @@
 
 namespace sk {
 
-constexpr int kTcBM = 128, kTcBN = 256, kTcBK = 64, kTcStages = 3, kTcMaxK = 256;
+constexpr int kTcBM = 128, kTcBN = 256, kTcBK = 64, kTcStages = 4, kTcMaxK = 256;
 constexpr int kTcSliceA = kTcBM * kTcBK * 2;                  // 16 KB
 constexpr int kTcSliceB = kTcBN * kTcBK * 2;                  // 32 KB
 constexpr int kTcStage = 32 * 128;                            // staging: 32 rows x 128 B
@@ -47,6 +47,9 @@ constexpr int kTcSmem =
     (kTcMaxK / kTcBK) * kTcSliceB + kTcStages * kTcSliceA + 4 * 2 * kTcStage + 1024;
 // streamed B: each stage of the ring holds an A slice and a B slice
 constexpr int kTcSmemStream = kTcStages * (kTcSliceA + kTcSliceB) + 4 * 2 * kTcStage + 1024;
+// both stay within the 227 KB a block may hold, with the kernel's ~1.2 KB of
+// static shared memory (barriers, bias)
+static_assert(kTcSmem + 1280 <= 232448 && kTcSmemStream + 1280 <= 232448, "shared memory");
 
 enum { kTcEpiF32 = 0, kTcEpiReluBf16 = 1, kTcEpiMaskBf16 = 2, kTcEpiBf16 = 3 };
 constexpr unsigned kTcWaitLimit = 1u << 24;                   // polls
