@@ -137,6 +137,66 @@ __host__ __device__ constexpr unsigned tc_idesc(int M, int N) {
          ((unsigned)(M >> 4) << 24);
 }
 
+// The 32 x kCols accumulator block of a warp's lane quarter at TMEM address
+// taddr (columns taddr .. taddr + kCols - 1) into v, 16 columns a load; no
+// wait (tcgen05.wait::ld before v is read).
+template <int kCols>
+__device__ __forceinline__ void tc_ld_slab(unsigned (&v)[kCols], unsigned taddr) {
+#pragma unroll
+  for (int h = 0; h < kCols / 16; ++h)
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+        "%12,%13,%14,%15}, [%16];"
+        : "=r"(v[h * 16 + 0]), "=r"(v[h * 16 + 1]), "=r"(v[h * 16 + 2]), "=r"(v[h * 16 + 3]),
+          "=r"(v[h * 16 + 4]), "=r"(v[h * 16 + 5]), "=r"(v[h * 16 + 6]), "=r"(v[h * 16 + 7]),
+          "=r"(v[h * 16 + 8]), "=r"(v[h * 16 + 9]), "=r"(v[h * 16 + 10]), "=r"(v[h * 16 + 11]),
+          "=r"(v[h * 16 + 12]), "=r"(v[h * 16 + 13]), "=r"(v[h * 16 + 14]), "=r"(v[h * 16 + 15])
+        : "r"(taddr + (unsigned)(h * 16)));
+}
+
+// One 128-byte-wide slab of a warp's 32 rows (accumulators v, waited; bias
+// b of its columns): converted (bf16 pairs rounded to nearest-even, element i
+// in the low half; or fp32), written into staging buffer (slab & 1) of the
+// warp in the layout a 128-byte-swizzled TMA store reads (row `lane`, 16-byte
+// chunk c at position c ^ (row & 7)) and stored at (x, y); the buffer's
+// previous store must have read it out first.
+template <int EPI, int kCols>
+__device__ __forceinline__ void tc_store_slab(const unsigned (&v)[kCols], const float* b,
+                                              unsigned char* stage0, unsigned slab, int lane,
+                                              const CUtensorMap* cmap, int x, int y) {
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+  __syncwarp();
+  unsigned char* st = stage0 + (slab & 1) * kTcStage;
+  unsigned w[32];
+#pragma unroll
+  for (int i = 0; i < kCols; i += 2) {
+    const float2 bb = *(const float2*)&b[i];
+    float f0 = __uint_as_float(v[i]) + bb.x, f1 = __uint_as_float(v[i + 1]) + bb.y;
+    if constexpr (EPI == kTcEpiF32) {
+      w[i] = __float_as_uint(f0);
+      w[i + 1] = __float_as_uint(f1);
+    } else {
+      if constexpr (EPI == kTcEpiReluBf16) {
+        f0 = fmaxf(f0, 0.f);
+        f1 = fmaxf(f1, 0.f);
+      }
+      const __nv_bfloat162 p = __floats2bfloat162_rn(f0, f1);
+      w[i / 2] = *(const unsigned*)&p;
+    }
+  }
+  const unsigned rbase = tc_smem_u32(st) + (unsigned)lane * 128u;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const unsigned addr = rbase + (unsigned)((c ^ (lane & 7)) * 16);
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w[4 * c]),
+                 "r"(w[4 * c + 1]), "r"(w[4 * c + 2]), "r"(w[4 * c + 3])
+                 : "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+  if (lane == 0) tc_tma_store(cmap, tc_smem_u32(st), x, y);
+}
+
 // EPI: kTcEpiF32 C = fp32 (acc + bias); kTcEpiReluBf16 C = bf16(relu(acc +
 // bias)); kTcEpiMaskBf16 C = bf16(acc) where aux > 0, else 0; kTcEpiBf16 C =
 // bf16(acc + bias).  STREAMB: the B
@@ -308,77 +368,102 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       asm volatile("tcgen05.fence::after_thread_sync;");
       const int n0 = nt * kTcBN, row0 = mt * kTcBM + q * 32;
       const int crow0 = ks * g.M + row0;             // a K split's partial goes to its own rows
+      if constexpr (EPI != kTcEpiMaskBf16) {
+        // software-pipelined: the next slab's accumulator loads are in flight
+        // while this slab is converted, staged and stored
+        const int nsl = (ncols + kCols - 1) / kCols;
+        unsigned va[kCols], vb[kCols];
+        tc_ld_slab<kCols>(va, tmem + ((unsigned)(q * 32) << 16) + (unsigned)(acc * kTcBN));
 #pragma unroll 1
-      for (int c0 = 0; c0 < ncols; c0 += kCols, ++slab) {
-        // the staging buffer of two slabs ago must have been read out
-        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-        __syncwarp();
-        unsigned char* st = stage0 + (slab & 1) * kTcStage;
-        // all loads of the slab first, one wait
-        unsigned v[kCols];
-#pragma unroll
-        for (int h = 0; h < kCols / 16; ++h) {       // 16 accumulator columns per load
-          const unsigned taddr =
-              tmem + ((unsigned)(q * 32) << 16) + (unsigned)(acc * kTcBN + c0 + h * 16);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
-              "%12,%13,%14,%15}, [%16];"
-              : "=r"(v[h * 16 + 0]), "=r"(v[h * 16 + 1]), "=r"(v[h * 16 + 2]), "=r"(v[h * 16 + 3]),
-                "=r"(v[h * 16 + 4]), "=r"(v[h * 16 + 5]), "=r"(v[h * 16 + 6]), "=r"(v[h * 16 + 7]),
-                "=r"(v[h * 16 + 8]), "=r"(v[h * 16 + 9]), "=r"(v[h * 16 + 10]),
-                "=r"(v[h * 16 + 11]), "=r"(v[h * 16 + 12]), "=r"(v[h * 16 + 13]),
-                "=r"(v[h * 16 + 14]), "=r"(v[h * 16 + 15])
-              : "r"(taddr));
-        }
-        // mask epilogue: this row's 64 auxiliary bf16 values of the slab
-        uint4 ax[EPI == kTcEpiMaskBf16 ? 8 : 1];
-        if constexpr (EPI == kTcEpiMaskBf16) {
-          const uint4* ap = (const uint4*)(g.aux + (size_t)(row0 + lane) * g.ldaux + n0 + c0);
-#pragma unroll
-          for (int c = 0; c < 8; ++c) ax[c] = __ldg(ap + c);
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-        unsigned w[32];                              // this row's 128 bytes of the slab
-        // bf16 results two at a time: one packed round-to-nearest-even
-        // conversion per pair (element i in the low half), the bias read as
-        // float2
-#pragma unroll
-        for (int i = 0; i < kCols; i += 2) {
-          if constexpr (EPI == kTcEpiMaskBf16) {
-            const unsigned word = (&ax[i / 8].x)[(i / 2) & 3];
-            const short h0 = (short)(word & 0xFFFFu), h1 = (short)(word >> 16);
-            const float f0 = h0 > 0 ? __uint_as_float(v[i]) : 0.f;      // aux > 0 (bf16 bits)
-            const float f1 = h1 > 0 ? __uint_as_float(v[i + 1]) : 0.f;
-            const __nv_bfloat162 p = __floats2bfloat162_rn(f0, f1);
-            w[i / 2] = *(const unsigned*)&p;
-          } else if constexpr (BF16) {
-            const float2 bb = *(const float2*)&sbias[c0 + i];
-            float f0 = __uint_as_float(v[i]) + bb.x, f1 = __uint_as_float(v[i + 1]) + bb.y;
-            if constexpr (EPI == kTcEpiReluBf16) {
-              f0 = fmaxf(f0, 0.f);
-              f1 = fmaxf(f1, 0.f);
-            }
-            const __nv_bfloat162 p = __floats2bfloat162_rn(f0, f1);
-            w[i / 2] = *(const unsigned*)&p;
-          } else {
-            const float2 bb = *(const float2*)&sbias[c0 + i];
-            w[i] = __float_as_uint(__uint_as_float(v[i]) + bb.x);
-            w[i + 1] = __float_as_uint(__uint_as_float(v[i + 1]) + bb.y);
+        for (int i = 0; i < nsl; i += 2) {
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+          if (i + 1 < nsl)
+            tc_ld_slab<kCols>(vb, tmem + ((unsigned)(q * 32) << 16) +
+                                      (unsigned)(acc * kTcBN + (i + 1) * kCols));
+          tc_store_slab<EPI, kCols>(va, sbias + i * kCols, stage0, slab++, lane, &cmap,
+                                    n0 + i * kCols, crow0);
+          if (i + 1 < nsl) {
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (i + 2 < nsl)
+              tc_ld_slab<kCols>(va, tmem + ((unsigned)(q * 32) << 16) +
+                                        (unsigned)(acc * kTcBN + (i + 2) * kCols));
+            tc_store_slab<EPI, kCols>(vb, sbias + (i + 1) * kCols, stage0, slab++, lane, &cmap,
+                                      n0 + (i + 1) * kCols, crow0);
           }
         }
-        // row `lane` of the slab, 16-byte chunk c at chunk position c ^ (row & 7)
-        // (the layout a 128-byte-swizzled TMA store reads)
-        const unsigned rbase = tc_smem_u32(st) + (unsigned)lane * 128u;
+      } else {
+#pragma unroll 1
+        for (int c0 = 0; c0 < ncols; c0 += kCols, ++slab) {
+          // the staging buffer of two slabs ago must have been read out
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          __syncwarp();
+          unsigned char* st = stage0 + (slab & 1) * kTcStage;
+          // all loads of the slab first, one wait
+          unsigned v[kCols];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const unsigned addr = rbase + (unsigned)((c ^ (lane & 7)) * 16);
-          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w[4 * c]),
-                       "r"(w[4 * c + 1]), "r"(w[4 * c + 2]), "r"(w[4 * c + 3])
-                       : "memory");
+          for (int h = 0; h < kCols / 16; ++h) {       // 16 accumulator columns per load
+            const unsigned taddr =
+                tmem + ((unsigned)(q * 32) << 16) + (unsigned)(acc * kTcBN + c0 + h * 16);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+                "%12,%13,%14,%15}, [%16];"
+                : "=r"(v[h * 16 + 0]), "=r"(v[h * 16 + 1]), "=r"(v[h * 16 + 2]), "=r"(v[h * 16 + 3]),
+                  "=r"(v[h * 16 + 4]), "=r"(v[h * 16 + 5]), "=r"(v[h * 16 + 6]), "=r"(v[h * 16 + 7]),
+                  "=r"(v[h * 16 + 8]), "=r"(v[h * 16 + 9]), "=r"(v[h * 16 + 10]),
+                  "=r"(v[h * 16 + 11]), "=r"(v[h * 16 + 12]), "=r"(v[h * 16 + 13]),
+                  "=r"(v[h * 16 + 14]), "=r"(v[h * 16 + 15])
+                : "r"(taddr));
+          }
+          // mask epilogue: this row's 64 auxiliary bf16 values of the slab
+          uint4 ax[EPI == kTcEpiMaskBf16 ? 8 : 1];
+          if constexpr (EPI == kTcEpiMaskBf16) {
+            const uint4* ap = (const uint4*)(g.aux + (size_t)(row0 + lane) * g.ldaux + n0 + c0);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) ax[c] = __ldg(ap + c);
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+          unsigned w[32];                              // this row's 128 bytes of the slab
+          // bf16 results two at a time: one packed round-to-nearest-even
+          // conversion per pair (element i in the low half), the bias read as
+          // float2
+#pragma unroll
+          for (int i = 0; i < kCols; i += 2) {
+            if constexpr (EPI == kTcEpiMaskBf16) {
+              const unsigned word = (&ax[i / 8].x)[(i / 2) & 3];
+              const short h0 = (short)(word & 0xFFFFu), h1 = (short)(word >> 16);
+              const float f0 = h0 > 0 ? __uint_as_float(v[i]) : 0.f;      // aux > 0 (bf16 bits)
+              const float f1 = h1 > 0 ? __uint_as_float(v[i + 1]) : 0.f;
+              const __nv_bfloat162 p = __floats2bfloat162_rn(f0, f1);
+              w[i / 2] = *(const unsigned*)&p;
+            } else if constexpr (BF16) {
+              const float2 bb = *(const float2*)&sbias[c0 + i];
+              float f0 = __uint_as_float(v[i]) + bb.x, f1 = __uint_as_float(v[i + 1]) + bb.y;
+              if constexpr (EPI == kTcEpiReluBf16) {
+                f0 = fmaxf(f0, 0.f);
+                f1 = fmaxf(f1, 0.f);
+              }
+              const __nv_bfloat162 p = __floats2bfloat162_rn(f0, f1);
+              w[i / 2] = *(const unsigned*)&p;
+            } else {
+              const float2 bb = *(const float2*)&sbias[c0 + i];
+              w[i] = __float_as_uint(__uint_as_float(v[i]) + bb.x);
+              w[i + 1] = __float_as_uint(__uint_as_float(v[i + 1]) + bb.y);
+            }
+          }
+          // row `lane` of the slab, 16-byte chunk c at chunk position c ^ (row & 7)
+          // (the layout a 128-byte-swizzled TMA store reads)
+          const unsigned rbase = tc_smem_u32(st) + (unsigned)lane * 128u;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const unsigned addr = rbase + (unsigned)((c ^ (lane & 7)) * 16);
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(w[4 * c]),
+                         "r"(w[4 * c + 1]), "r"(w[4 * c + 2]), "r"(w[4 * c + 3])
+                         : "memory");
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) tc_tma_store(&cmap, tc_smem_u32(st), n0 + c0, crow0);
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) tc_tma_store(&cmap, tc_smem_u32(st), n0 + c0, crow0);
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
       tc_arrive(tc_smem_u32(&acce_bar[acc]));
