@@ -363,7 +363,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // 0: ld = cols); boxes of 128 bytes x box_rows, 128-byte swizzle.  A TMA
 // store writes only the part of a box inside the map.
 static bool encode_map(CUtensorMap* map, const void* ptr, int esize, int rows, int cols,
-                       int box_rows, int ld = 0) {
+                       int box_rows, int ld = 0, bool promote256 = true) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
@@ -372,12 +372,15 @@ static bool encode_map(CUtensorMap* map, const void* ptr, int esize, int rows, i
   const cuuint32_t estr[2] = {1, 1};
   return enc(map, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
              2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_SWIZZLE_128B,
+             promote256 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 static bool make_tc_maps(Mlp& m) {
-  return encode_map(&m.tmA[0], m.X, 2, m.max_batch, m.K1, kTcBM) &&
+  // X: the first layer reads the first K1f (64 for n <= 32) of each row's
+  // K1 = 128 columns, so its loads are promoted in L2 by 128 bytes only
+  return encode_map(&m.tmA[0], m.X, 2, m.max_batch, m.K1, kTcBM, 0, m.K1f >= m.K1) &&
          encode_map(&m.tmA[1], m.H1, 2, m.max_batch, kHidden, kTcBM) &&
          encode_map(&m.tmA[2], m.H2, 2, m.max_batch, kHidden, kTcBM) &&
          encode_map(&m.tmB[0], m.W1t, 2, kHidden, m.K1, kTcBN) &&
