@@ -110,6 +110,38 @@ def test_learned_chains_are_exact(variant, n):
     assert abs(est / (oracle.backtrack_count(variant, n) / 2) - 1) < 0.02
 
 
+@pytest.mark.parametrize("variant,n", [(0, 5), (1, 4)])
+def test_learned_chains_exact_when_the_row_maximum_underflows(variant, n):
+    # Logits of -100 on every move (W3 = 0, b3 = -100) while the padding
+    # columns inside the move table's last 8-move word stay 0 (n = 5 Skolem:
+    # 35 moves, Langford n = 4: 18): the step kernel's unmasked shift, the
+    # row's largest element, is then 0 and every valid weight e^-100
+    # underflows, so it must take the valid moves' maximum instead.  The
+    # proposal is uniform over the valid moves and the chains must still
+    # sample the exact Boltzmann weights.
+    d = si.differences(variant, n)
+    _, nslot = mlp_ref.move_table(n, d)
+    nm = int(nslot.sum())
+    assert nm % 8
+    rng = np.random.default_rng(5)
+    params = [rng.normal(0.0, 0.1, (2 * n, 256)), np.zeros(256), rng.normal(0.0, 0.1, (256, 256)),
+              np.zeros(256), np.zeros((256, nm)), np.full(nm, -100.0)]
+    model = sk.Mlp(variant, n, 8192, seed=4)
+    model.set_params(_flat(params))
+    beta = np.array([0.0, 0.7, 1.5, 2.6, 4.0, 6.0, 9.0, 14.0])
+    res = sk.pt_run(variant, n, beta, 1024, 20000, 10000, 23, model=model)
+    model.check()
+    model.close()
+    N = oracle.simplified_energy_hist(variant, n).astype(np.float64)
+    E = np.arange(2 * n + 1)
+    for j in range(len(beta)):
+        p = N * np.exp(-beta[j] * E)
+        p /= p.sum()
+        h = res["hist"][j].astype(np.float64)
+        assert np.abs(h / h.sum() - p).max() < 0.01, (j, h / h.sum(), p)
+    assert res["acc_move"].min() > 0
+
+
 @pytest.mark.parametrize("variant,n,batch", [(1, 20, 4096), (1, 20, 65536), (0, 24, 40000)])
 def test_tensor_memory_and_mma_sync_paths_agree(variant, n, batch):
     # the two forward GEMM paths see the same bf16 operands; their fp32 sums
