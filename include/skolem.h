@@ -414,7 +414,9 @@ int sk_mlp_set_gemm(void *model, int use_tensor_memory_path);
 int sk_mlp_check(void *model);
 /* The learned tempering run behind pt_estimate_ex with SK_PT_LEARNED, with
  * the outputs of sk_pt_run (no final states).  Needs a model of the same
- * (variant, n) whose max_batch >= L * M rounded up to 128. */
+ * (variant, n) whose max_batch >= L * M rounded up to 128.  The exchanges of
+ * each iteration run on a second stream the call creates, joined to the
+ * run's stream by events; the call returns after both have finished. */
 int sk_pt_run_learned(int variant, int n, int M, const double *beta, int L, uint64_t iters,
                       uint64_t burnin, uint64_t seed, const void *model, uint64_t *hist,
                       uint64_t *acc_move, uint64_t *acc_swap);
