@@ -142,6 +142,47 @@ def test_learned_chains_exact_when_the_row_maximum_underflows(variant, n):
     assert res["acc_move"].min() > 0
 
 
+def _hot_energy_distribution(variant, n, samples, seed):
+    # The energy (empty bins) of the simplified problem at beta = 0: every pair
+    # at an independent uniform start slot, straight from the definition.
+    d = si.differences(variant, n)
+    rng = np.random.default_rng(seed)
+    counts = np.zeros(2 * n + 1)
+    chunk = 250_000
+    rows = np.arange(chunk)
+    for _ in range(samples // chunk):
+        occ = np.zeros((chunk, 2 * n), np.int8)
+        for dk in d:
+            s = rng.integers(0, 2 * n - dk, chunk)
+            occ[rows, s] += 1
+            occ[rows, s + dk] += 1
+        counts += np.bincount((occ == 0).sum(1), minlength=2 * n + 1)
+    return counts / counts.sum()
+
+
+@pytest.mark.parametrize("variant,n", [(0, 16), (0, 20), (1, 24)])
+def test_learned_chains_sample_boltzmann_over_several_chunks(variant, n):
+    # Move tables of 376, 590 and 828 moves: two, three and four 256-move
+    # chunks a row (the draw's lane and chunk selection, reverse moves in
+    # later chunks, rows staged in shared memory, the bound that rejects
+    # without a row).  At the hot rungs P_beta(E) is proportional to
+    # P_0(E) e^(-beta E), P_0 sampled from the definition (2e6 draws); an
+    # untrained network proposes.
+    p0 = _hot_energy_distribution(variant, n, 2_000_000, 17)
+    beta = np.array([0.0, 0.3, 0.6, 1.0])
+    model = sk.Mlp(variant, n, 4096 * 4, seed=3)
+    res = sk.pt_run(variant, n, beta, 4096, 2000, 500, 31, model=model)
+    model.check()
+    model.close()
+    E = np.arange(2 * n + 1)
+    for j, b in enumerate(beta):
+        p = p0 * np.exp(-b * E)
+        p /= p.sum()
+        h = res["hist"][j].astype(np.float64)
+        assert np.abs(h / h.sum() - p).max() < 0.01, (j, np.abs(h / h.sum() - p).max())
+    assert (res["acc_move"] > 0).all() and (res["acc_swap"][:-1] > 0).all()
+
+
 @pytest.mark.parametrize("variant,n,batch", [(1, 20, 4096), (1, 20, 65536), (0, 24, 40000)])
 def test_tensor_memory_and_mma_sync_paths_agree(variant, n, batch):
     # the two forward GEMM paths see the same bf16 operands; their fp32 sums
