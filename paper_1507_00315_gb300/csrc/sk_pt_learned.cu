@@ -401,8 +401,8 @@ __device__ __forceinline__ void load_step_in(const LearnedDev& d, const __nv_bfl
 // first: the states in Zp are the chains' initial ones, taken unconditionally
 // (nothing to test; nothing is stored yet), and the draw is iteration 0's;
 // count0 counts their energies as iteration 0's statistics.  propose = 0: no
-// draw (the last iteration).  Dynamic shared memory: two row buffers per warp
-// (lt_step_smem).
+// draw (the last iteration).  Dynamic shared memory: two stagings per warp
+// (StepBuf: proposed row, current row, current sums; lt_step_smem).
 template <int CH>
 __host__ __device__ constexpr int lt_step_smem() {
   return 8 * 2 * (int)sizeof(StepBuf<CH>);
