@@ -5,6 +5,8 @@ size, symmetry, convention) and the tempering runs (variant, order, ladder,
 iteration counts)."""
 import math
 
+import numpy as np
+
 import pytest
 
 import paper_1507_00315_gb300 as sk
@@ -113,3 +115,12 @@ def test_extended_refusals_before_device_work():
         with pytest.raises(sk.SkolemError) as e:
             sk.extended_item_residues(12, hole, 9, 0, 1, sk.default_primes()[:3])
         assert e.value.status == sk.SK_EINVAL
+
+
+def test_network_forwards_refuse_a_null_model():
+    # both forwards check their arguments before any device work
+    L = sk.lib()
+    slots = np.zeros(64, np.uint8)
+    for fn, out in ((L.sk_mlp_forward, np.zeros(64, np.float32)),
+                    (L.sk_mlp_forward_bf16, np.zeros(64, np.uint16))):
+        assert fn(None, slots.ctypes.data, 1, out.ctypes.data) == sk.SK_EINVAL
