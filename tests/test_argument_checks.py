@@ -6,7 +6,6 @@ iteration counts)."""
 import math
 
 import numpy as np
-
 import pytest
 
 import paper_1507_00315_gb300 as sk
