@@ -64,6 +64,9 @@ struct TcGemmArgs {
   int ldaux;
   int nvalid;                     // > 0: only columns < nvalid are wanted (the last column
                                   // tile multiplies and stores that many, rounded up to 16)
+  int pdl;                        // launch as a programmatic dependent of the previous kernel
+                                  // of the stream; only where B is not written by it or by any
+                                  // kernel since the last ordinary launch
 };
 
 __device__ __forceinline__ unsigned tc_smem_u32(const void* p) {
@@ -253,6 +256,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const unsigned tmem = tmem_base_s;
+  // the next kernel of the stream may start its own set-up now (it waits
+  // for this grid's completion before it reads what this grid writes)
+  asm volatile("griddepcontrol.launch_dependents;");
 
   if (warp == 0) {
     // ---------------------------------------------------------------- TMA producer
@@ -266,6 +272,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int kb = 0; kb < nkb; ++kb)
           tc_tma_load(tc_smem_u32(sB + kb * kTcSliceB), &bmap, (kb0 + kb) * kTcBK, nt * kTcBN, bb);
       }
+      // launched as a programmatic dependent (g.pdl): the previous kernel's
+      // results (A) only after it has completed; resident weights (B) may
+      // come earlier, as they do not change between such launches (a no-op
+      // for an ordinary launch)
+      asm volatile("griddepcontrol.wait;" ::: "memory");
       unsigned u = 0;                                // slices issued
       for (int t = 0; t < my_tiles && ok; ++t) {
         const int mt = m_first + t * groups;

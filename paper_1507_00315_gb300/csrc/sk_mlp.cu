@@ -447,6 +447,8 @@ cudaError_t gemm_tc_launch(const TcGemmArgs& g, const CUtensorMap& amap, const C
   if (per < 1) per = 1;
   if (per > MT) per = MT;
   const int grid = per * NT * KS;
+  if (g.pdl) return launch_dependent(gemm_tc_kernel<EPI, STREAMB>, grid, kTcThreads,
+                                     STREAMB ? kTcSmemStream : kTcSmem, s, amap, bmap, cmap, g);
   gemm_tc_kernel<EPI, STREAMB><<<grid, kTcThreads, STREAMB ? kTcSmemStream : kTcSmem, s>>>(
       amap, bmap, cmap, g);
   return cudaGetLastError();
@@ -463,7 +465,8 @@ cudaError_t gemm_tc(const TcGemmArgs& g, const CUtensorMap& amap, const CUtensor
 
 // Forward pass for B (multiple of 128) states whose slots are already in
 // m.slots: X, H1, H2 (bf16) and Z (fp32 logits, or bf16 with logits_bf16).
-cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s, bool logits_bf16, bool inputs_ready) {
+cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s, bool logits_bf16, bool inputs_ready,
+                            cudaEvent_t before_l2, bool dependent) {
   if (!inputs_ready)
     mlp_inputs_kernel<<<(B + 7) / 8, 256, 0, s>>>(m.slots, B, m.n, m.delta, m.K1, m.X);
   if (m.use_tc) {
@@ -474,8 +477,9 @@ cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s, bool logits_bf16, boo
     std::memset(&t, 0, sizeof(t));
     t.M = B; t.N = kHidden; t.K = m.K1f; t.bias = m.b1; t.err = m.tc_err;
     e = gemm_tc(t, m.tmA[0], m.tmB[0], m.tmC[0], kTcEpiReluBf16, s);
+    if (e == cudaSuccess && before_l2) e = cudaStreamWaitEvent(s, before_l2, 0);
     if (e != cudaSuccess) return e;
-    t.K = kHidden; t.bias = m.b2;
+    t.K = kHidden; t.bias = m.b2; t.pdl = dependent ? 1 : 0;
     e = gemm_tc(t, m.tmA[1], m.tmB[1], m.tmC[1], kTcEpiReluBf16, s);
     if (e != cudaSuccess) return e;
     t.N = m.NMp; t.bias = m.b3;
@@ -488,6 +492,7 @@ cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s, bool logits_bf16, boo
   g.M = B; g.N = kHidden; g.K = m.K1f; g.A = m.X; g.lda = m.K1; g.B = m.W1; g.ldb = kHidden;
   g.C = m.H1; g.ldc = kHidden; g.bias = m.b1;
   cudaError_t e = gemm<false, false, EPI_BF16_RELU>(g, 1, s);
+  if (e == cudaSuccess && before_l2) e = cudaStreamWaitEvent(s, before_l2, 0);
   if (e != cudaSuccess) return e;
   g.K = kHidden; g.A = m.H1; g.lda = kHidden; g.B = m.W2; g.C = m.H2; g.bias = m.b2;
   e = gemm<false, false, EPI_BF16_RELU>(g, 1, s);

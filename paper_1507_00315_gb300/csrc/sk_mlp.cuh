@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <utility>
 
 #include "sk_pt.cuh"
 
@@ -87,9 +88,33 @@ __device__ __forceinline__ float warp_sum(float v) {
 // Forward pass for B (multiple of 128) states whose start slots are in
 // m.slots: X, H1, H2 (bf16) and the logits Z (fp32, [B][NMp]; with
 // logits_bf16, bf16 [B][NMp] in the first half of Z's memory).  With
-// inputs_ready the caller has already written the input rows X.
+// inputs_ready the caller has already written the input rows X.  before_l2:
+// an event the stream waits for between the first and the second layer.
+// dependent: the second and third layers are launched as programmatic
+// dependents of the layer before (they may set up while it finishes; only
+// while the weights stay unchanged, as in a tempering run).
 cudaError_t mlp_forward_dev(Mlp& m, int B, cudaStream_t s, bool logits_bf16 = false,
-                            bool inputs_ready = false);
+                            bool inputs_ready = false, cudaEvent_t before_l2 = nullptr,
+                            bool dependent = false);
+
+// Launch of kernel k as a programmatic dependent of the previous kernel of
+// stream s (it must execute griddepcontrol.wait before it reads what that
+// kernel writes).
+template <class... KArgs, class... Args>
+cudaError_t launch_dependent(void (*k)(KArgs...), int grid, int block, size_t smem,
+                             cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
 MoveTable move_table(const Mlp& m);
 
 }  // namespace sk

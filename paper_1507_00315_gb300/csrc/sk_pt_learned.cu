@@ -417,9 +417,14 @@ __global__ void __launch_bounds__(256, CH <= 3 ? 3 : 2)
   __shared__ unsigned s_bits[8][kLtChunks * 8];
   __shared__ float s_beta[kPtMaxRungsLearned];
   extern __shared__ __align__(16) unsigned char s_dyn[];   // [warp][2] StepBuf
+  // launched as a programmatic dependent of the forward's last layer: the
+  // next kernel may set up now; the tables above are not written by the
+  // forward, its logits are read only after it has completed
+  asm volatile("griddepcontrol.launch_dependents;");
   copy_move_maps(d.maps, mm);
   for (int i = threadIdx.x; i < d.M; i += blockDim.x) s_beta[i] = (float)d.beta[i];
   __syncthreads();
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, li = lane & 7;
   const int NM = mt.NM, stride = gridDim.x * 8;
   const bool fst = first != 0;
@@ -792,23 +797,26 @@ int pt_learned_run(int variant, int n, int M, const double* beta, int L, uint64_
                                        iters > 0 && burnin == 0 ? 1 : 0, m->slots, Zb, m->X, m->K1);
     e = cudaGetLastError();
   }
-  // The exchanges of iteration t run on a side stream beside the forward of
-  // iteration t + 1 (which reads only the input rows and the weights); the
-  // step kernel of t + 1 waits for them (it reads the rungs and writes the
-  // energies they read).
+  // The exchanges of iteration t run on a side stream beside the first layer
+  // of iteration t + 1 (which reads only the input rows and the weights); the
+  // stream joins them before the second layer, ahead of the step kernel of
+  // t + 1 (it reads the rungs and writes the energies they read).
   cudaStream_t xs = nullptr;
   cudaEvent_t ev_step = nullptr, ev_exch = nullptr;
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&xs, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_step, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_exch, cudaEventDisableTiming);
+  // Per iteration: layer 1, the join with the previous exchanges, layers 2
+  // and 3 and the step kernel each launched as a programmatic dependent of
+  // the kernel before it (it sets up while that one finishes).
   for (uint64_t t = 0; t < iters && e == cudaSuccess; ++t) {
-    e = mlp_forward_dev(*m, Bp, s, true, true);     // the step kernel wrote the input rows
-    if (e == cudaSuccess && t > 0) e = cudaStreamWaitEvent(s, ev_exch, 0);
+    // the step kernel wrote the input rows
+    e = mlp_forward_dev(*m, Bp, s, true, true, t > 0 ? ev_exch : nullptr, true);
     if (e != cudaSuccess) break;
     const bool more = t + 1 < iters;
-    lk.step<<<chain_grid, 256, lk.smem, s>>>(d, mt, (unsigned)t, 0, more ? 1 : 0, 0, m->slots, Zb, m->X,
-                                       m->K1);
-    e = cudaEventRecord(ev_step, s);
+    e = launch_dependent(lk.step, chain_grid, 256, (size_t)lk.smem, s, d, mt, (unsigned)t, 0,
+                         more ? 1 : 0, 0, m->slots, Zb, m->X, m->K1);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_step, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(xs, ev_step, 0);
     if (e != cudaSuccess) break;
     lt_exchange_kernel<<<(L + 3) / 4, 128, 0, xs>>>(d, (unsigned)t,
