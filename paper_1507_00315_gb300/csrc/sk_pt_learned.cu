@@ -32,7 +32,8 @@ struct LearnedDev {
   int* lor;                  // [L][M]: configuration holding rung j
   __nv_bfloat16* Zcur;       // [B][NMp] logits of the current states (bf16)
   float* lse;                // [B] log-normaliser over their valid moves
-  float* mx;                 // [B] the shift of their stored weight sums (the row's maximum)
+  float* mx;                 // [B] the shift of their stored weight sums (the row's largest
+                             //   element; its valid moves' maximum where that underflows)
   float* parts;              // [B][CH][32] per lane and chunk: sum of e^(z - mx) over the
                              //   lane's valid moves of the chunk (the current state's)
   int4* prop;                // [B] (k | old slot << 8 | new slot << 16, dE, log q(C' | C)
