@@ -403,63 +403,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
         }
       } else {
+        // the masked epilogue also reads this row's 64 auxiliary bf16 values
+        // of each slab (C = acc where aux > 0): one slab at a time
 #pragma unroll 1
         for (int c0 = 0; c0 < ncols; c0 += kCols, ++slab) {
           // the staging buffer of two slabs ago must have been read out
           if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
           __syncwarp();
           unsigned char* st = stage0 + (slab & 1) * kTcStage;
-          // all loads of the slab first, one wait
           unsigned v[kCols];
+          tc_ld_slab<kCols>(v, tmem + ((unsigned)(q * 32) << 16) + (unsigned)(acc * kTcBN + c0));
+          uint4 ax[8];
+          const uint4* ap = (const uint4*)(g.aux + (size_t)(row0 + lane) * g.ldaux + n0 + c0);
 #pragma unroll
-          for (int h = 0; h < kCols / 16; ++h) {       // 16 accumulator columns per load
-            const unsigned taddr =
-                tmem + ((unsigned)(q * 32) << 16) + (unsigned)(acc * kTcBN + c0 + h * 16);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
-                "%12,%13,%14,%15}, [%16];"
-                : "=r"(v[h * 16 + 0]), "=r"(v[h * 16 + 1]), "=r"(v[h * 16 + 2]), "=r"(v[h * 16 + 3]),
-                  "=r"(v[h * 16 + 4]), "=r"(v[h * 16 + 5]), "=r"(v[h * 16 + 6]), "=r"(v[h * 16 + 7]),
-                  "=r"(v[h * 16 + 8]), "=r"(v[h * 16 + 9]), "=r"(v[h * 16 + 10]),
-                  "=r"(v[h * 16 + 11]), "=r"(v[h * 16 + 12]), "=r"(v[h * 16 + 13]),
-                  "=r"(v[h * 16 + 14]), "=r"(v[h * 16 + 15])
-                : "r"(taddr));
-          }
-          // mask epilogue: this row's 64 auxiliary bf16 values of the slab
-          uint4 ax[EPI == kTcEpiMaskBf16 ? 8 : 1];
-          if constexpr (EPI == kTcEpiMaskBf16) {
-            const uint4* ap = (const uint4*)(g.aux + (size_t)(row0 + lane) * g.ldaux + n0 + c0);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) ax[c] = __ldg(ap + c);
-          }
+          for (int c = 0; c < 8; ++c) ax[c] = __ldg(ap + c);
           asm volatile("tcgen05.wait::ld.sync.aligned;");
           unsigned w[32];                              // this row's 128 bytes of the slab
-          // bf16 results two at a time: one packed round-to-nearest-even
-          // conversion per pair (element i in the low half), the bias read as
-          // float2
+          // two results at a time, one packed round-to-nearest-even
+          // conversion per pair (element i in the low half)
 #pragma unroll
           for (int i = 0; i < kCols; i += 2) {
-            if constexpr (EPI == kTcEpiMaskBf16) {
-              const unsigned word = (&ax[i / 8].x)[(i / 2) & 3];
-              const short h0 = (short)(word & 0xFFFFu), h1 = (short)(word >> 16);
-              const float f0 = h0 > 0 ? __uint_as_float(v[i]) : 0.f;      // aux > 0 (bf16 bits)
-              const float f1 = h1 > 0 ? __uint_as_float(v[i + 1]) : 0.f;
-              const __nv_bfloat162 p = __floats2bfloat162_rn(f0, f1);
-              w[i / 2] = *(const unsigned*)&p;
-            } else if constexpr (BF16) {
-              const float2 bb = *(const float2*)&sbias[c0 + i];
-              float f0 = __uint_as_float(v[i]) + bb.x, f1 = __uint_as_float(v[i + 1]) + bb.y;
-              if constexpr (EPI == kTcEpiReluBf16) {
-                f0 = fmaxf(f0, 0.f);
-                f1 = fmaxf(f1, 0.f);
-              }
-              const __nv_bfloat162 p = __floats2bfloat162_rn(f0, f1);
-              w[i / 2] = *(const unsigned*)&p;
-            } else {
-              const float2 bb = *(const float2*)&sbias[c0 + i];
-              w[i] = __float_as_uint(__uint_as_float(v[i]) + bb.x);
-              w[i + 1] = __float_as_uint(__uint_as_float(v[i + 1]) + bb.y);
-            }
+            const unsigned word = (&ax[i / 8].x)[(i / 2) & 3];
+            const short h0 = (short)(word & 0xFFFFu), h1 = (short)(word >> 16);
+            const float f0 = h0 > 0 ? __uint_as_float(v[i]) : 0.f;      // aux > 0 (bf16 bits)
+            const float f1 = h1 > 0 ? __uint_as_float(v[i + 1]) : 0.f;
+            const __nv_bfloat162 p = __floats2bfloat162_rn(f0, f1);
+            w[i / 2] = *(const unsigned*)&p;
           }
           // row `lane` of the slab, 16-byte chunk c at chunk position c ^ (row & 7)
           // (the layout a 128-byte-swizzled TMA store reads)
